@@ -1,0 +1,98 @@
+"""Pins for the oracle's series preparation (Section 2.3): downsampling, the
+running-median dereddening, and FP64 normalisation / int8 quantisation.
+
+Expected values: brute-force medians per window (numpy), exact closed forms
+for monotone and linear series, and invariants of the normalised series.
+"""
+import numpy as np
+import pytest
+
+
+def brute_runmed(x: np.ndarray, w: int) -> np.ndarray:
+    h = w // 2
+    n = x.size
+    return np.array([np.median(x[max(0, i - h): min(n, i + h + 1)]) for i in range(n)])
+
+
+def test_downsample_sums(orc):
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(1001).astype(np.float32)
+    y = orc.downsample(x, 2)
+    assert y.size == 500
+    np.testing.assert_array_equal(y, x[:1000:2].astype(np.float64) + x[1:1000:2])
+    u = rng.integers(0, 256, 999).astype(np.uint8)
+    y8 = orc.downsample(u, 64)
+    assert y8.size == 15
+    assert np.array_equal(y8, u[:960].reshape(15, 64).sum(axis=1).astype(np.float64))
+
+
+@pytest.mark.parametrize("n,w", [(50, 1), (50, 3), (200, 17), (333, 101), (64, 1025), (1000, 999)])
+def test_running_median_matches_brute(orc, n, w):
+    rng = np.random.default_rng(n + w)
+    x = rng.standard_normal(n)
+    ref = brute_runmed(x, w)
+    assert np.array_equal(orc.running_median(x, w), ref)
+    idx = np.arange(0, n, 7)
+    assert np.array_equal(orc.running_median_at(x, w, idx), ref[idx])
+
+
+def test_running_median_with_ties(orc):
+    rng = np.random.default_rng(9)
+    x = rng.integers(-3, 4, size=500).astype(np.float64)
+    for w in [5, 51, 201]:
+        assert np.array_equal(orc.running_median(x, w), brute_runmed(x, w))
+
+
+def test_running_median_monotone_and_linear(orc):
+    """A monotone series' window median is the centre sample away from the ends,
+    so a linear trend is removed exactly there."""
+    n, w = 400, 41
+    x = 3.0 * np.arange(n) + 7.0
+    med = orc.running_median(x, w)
+    h = w // 2
+    assert np.array_equal(med[h:n - h], x[h:n - h])
+    # at the ends the truncated window's median: the mean of its two middles when even
+    assert med[0] == np.median(x[:h + 1])
+    xs = np.sin(np.arange(n) * 0.001)  # monotone increasing on this range
+    assert np.array_equal(orc.running_median(xs, w)[h:n - h], xs[h:n - h])
+
+
+def test_window_one_is_identity(orc):
+    x = np.random.default_rng(1).standard_normal(77)
+    assert np.array_equal(orc.running_median(x, 1), x)
+
+
+def test_normalise_invariants(orc):
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal(10000) * 3.7 + 11.0
+    z64, z32, q, mean, std, deg = orc.normalise(r)
+    assert not deg
+    assert abs(z64.mean()) < 1e-12 and abs(z64.std() - 1.0) < 1e-12
+    assert np.array_equal(z32, z64.astype(np.float32))
+    # int8 code: 16 z rounded, clipped to +-127
+    inside = np.abs(16 * z64) < 126.5
+    assert np.all(np.abs(q[inside] / 16.0 - z64[inside]) <= 1 / 32 + 1e-15)
+    big = np.concatenate([np.zeros(1000), [1e6, -1e6]])
+    _, _, qb, _, _, _ = orc.normalise(big)
+    assert qb[-2] == 127 and qb[-1] == -127
+
+
+def test_quantise_half_to_even(orc):
+    """16 z exactly on a half-integer rounds to the even neighbour."""
+    # mean 0, population std 1: values +-1 (x4) and the probes below
+    r = np.array([2.5 / 16, -2.5 / 16, 3.5 / 16, -3.5 / 16])
+    s = np.sqrt(np.mean(r * r))
+    # rescale so the std is exactly representable: use the normalised z directly
+    z64, _, q, _, std, _ = orc.normalise(r)
+    got = {float(v): int(c) for v, c in zip(16 * z64, q)}
+    for v, c in got.items():
+        frac = abs(v) - np.floor(abs(v))
+        if abs(frac - 0.5) < 1e-12:
+            assert c % 2 == 0
+        assert abs(c - v) <= 0.5 + 1e-12
+    assert s > 0 and std > 0
+
+
+def test_constant_series_degenerate(orc):
+    z64, z32, q, mean, std, deg = orc.normalise(np.full(100, 5.0))
+    assert deg and std == 0.0 and not z32.any() and not q.any()
