@@ -1,0 +1,213 @@
+/*
+ * ffa.h -- C ABI of the GB300-native Fast Folding Algorithm period search.
+ *
+ * The method is the FFA search of Cameron et al. 2017 (MNRAS, "An
+ * investigation of pulsar searching techniques with the Fast Folding
+ * Algorithm"): a dedispersed time series is optionally pre-downsampled,
+ * dereddened with a running median, normalised, folded at every base period
+ * P0 by the Staelin FFA (Section 2.1, Eq. 1-2) over octaves of period with
+ * downsampling by two per octave (Section 2.3), and every folded profile is
+ * scored by Algorithm 1, the MAD-normalised power-of-two boxcar matched
+ * filter (Section 2.2.1, Eq. 3-4).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named d_* are device pointers on the current CUDA device;
+ *     pointers without the prefix are host pointers.  The caller owns all
+ *     memory; the library allocates nothing on the device or the host heap
+ *     outside ffa_plan_create (which allocates the opaque plan on the host).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *     Device work is enqueued asynchronously on it; inputs must stay valid
+ *     and unmodified until that work completes.
+ *   - Every call returns an ffa_status and never aborts, prints or exits.
+ *     On failure ffa_last_error() returns a message for the calling thread.
+ *     Argument errors are detected on the host before any launch.  Checks
+ *     that only the device can make (e.g. an internal selection invariant)
+ *     set the int32 word *d_status to a non-zero ffa_status; read it after
+ *     the stream completes (ffa_wait does this with a bounded wait).
+ *   - Layouts are row-major and densely packed (no row pitch).
+ *   - Plans are immutable after creation; one plan may be used concurrently
+ *     from several host threads on different streams and workspaces.
+ */
+#ifndef FFA_GB300_H
+#define FFA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FFA_OK = 0,
+    FFA_ERR_ARG = 1,         /* invalid argument (host check)                      */
+    FFA_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed               */
+    FFA_ERR_OOM = 3,         /* caller-provided buffer too small                   */
+    FFA_ERR_TIMEOUT = 4,     /* a bounded wait expired                             */
+    FFA_ERR_CANCELLED = 5,   /* reserved for the serving layer                     */
+    FFA_ERR_UNSUPPORTED = 6, /* valid request outside the implemented envelope     */
+    FFA_ERR_DEVICE = 7       /* a device-side invariant check failed               */
+} ffa_status;
+
+/* Input sample type: 32-bit float (PRESTO-style) or 8-bit unsigned
+ * (SIGPROC-style) series, the two formats ffancy reads (Section 2.3). */
+typedef enum { FFA_IN_F32 = 0, FFA_IN_U8 = 1, FFA_IN_F64 = 2 } ffa_input_type;
+
+/* Fold precision: FP32 adds of the FP32-rounded normalised series, or exact
+ * int32 adds of an int8 code q = clip(rint(16 z), -127, 127). */
+typedef enum { FFA_FOLD_F32 = 0, FFA_FOLD_I8 = 1 } ffa_fold_precision;
+
+/* Search configuration (ffancy's interface, Section 2.3; periods in seconds). */
+typedef struct {
+    double tsamp_s;          /* sampling interval of the input series            */
+    double period_min_s;     /* search range [period_min_s, period_max_s)        */
+    double period_max_s;
+    double duty_max;         /* widths 1,2,4,.. up to the first > duty_max * P0
+                                (Section 2.2.1 uses 0.2); ignored if fixed widths */
+    int32_t downsample0;     /* pre-downsampling factor D0 >= 1                  */
+    int32_t detrend_window;  /* running-median window in samples; 0 = the paper's
+                                default min(2 Pmax, 4 Pmin); < 0 = no dereddening;
+                                made odd by W |= 1                                */
+    int32_t min_rows;        /* skip P0 with fewer data rows (0 -> 2)            */
+    int32_t in_type;         /* ffa_input_type                                   */
+    int32_t precision;       /* ffa_fold_precision                               */
+    int32_t n_widths_fixed;  /* > 0: use widths_fixed[0..n) instead of duty_max  */
+    int32_t widths_fixed[16];
+} ffa_search_config;
+
+/* One periodogram record per trial period (16 bytes).  flags bit 0: the
+ * profile's MAD was zero (S/N reported as 0). */
+typedef struct {
+    float snr;      /* Algorithm 1 score: max over widths and phases             */
+    int32_t width;  /* boxcar width (bins) of the best score                     */
+    int32_t phase;  /* first bin of the best boxcar window                        */
+    uint32_t flags;
+} ffa_record;
+
+/* One base period of the plan.  Trial k of this entry (0 <= k < m_rows) is
+ * periodogram record first_trial + k and has period
+ * (p0 + k / (m_rows - 1)) * tsamp * D0 * 2^octave  (Eq. 2 with N = M * P0). */
+typedef struct {
+    int32_t octave;
+    int32_t p0;          /* bins per folded profile                             */
+    int32_t m_data;      /* floor(n_octave / p0) data rows                      */
+    int32_t m_rows;      /* next power of two >= m_data; rows beyond are zero   */
+    int32_t n_widths;
+    int32_t widths[16];
+    int32_t pad;
+    int64_t n_octave;    /* samples of this octave's series                     */
+    int64_t first_trial;
+} ffa_plan_entry;
+
+/* A candidate returned by ffa_candidates. */
+typedef struct {
+    int64_t trial;      /* periodogram index                                     */
+    double period_s;
+    float snr;
+    int32_t octave, p0, k, width, phase;
+} ffa_candidate;
+
+typedef struct ffa_plan ffa_plan;
+
+/* ---- plan ---------------------------------------------------------------- */
+
+/* Build the search plan for a series of n input samples (host only, no
+ * device work): octaves, base periods, row counts, widths and the workspace
+ * size.  Errors: FFA_ERR_ARG for a non-positive tsamp/period range/D0, an
+ * empty plan is allowed (zero trials). */
+ffa_status ffa_plan_create(const ffa_search_config* cfg, int64_t n, ffa_plan** out);
+void ffa_plan_destroy(ffa_plan* plan);
+
+/* Sizes of a plan: base periods, periodogram length, octaves, the odd
+ * running-median window and the bytes of device workspace ffa_search needs. */
+ffa_status ffa_plan_info(const ffa_plan* plan, int64_t* n_periods, int64_t* n_trials,
+                         int32_t* n_octaves, int32_t* window, size_t* workspace_bytes);
+
+/* Copy the first `cap` plan entries (periodogram order) to host memory. */
+ffa_status ffa_plan_entries(const ffa_plan* plan, ffa_plan_entry* out, int64_t cap);
+
+/* ---- the search ------------------------------------------------------------ */
+
+/* Run the whole search (Section 2.3 pipeline) on the n-sample device series
+ * d_series (type cfg.in_type).  Writes n_trials records to d_records.
+ * d_workspace: >= workspace_bytes of device memory, 256-byte aligned.
+ * d_status: one int32 device word, zeroed by the caller; device-side checks
+ * store an ffa_status there.  Asynchronous on `stream`. */
+ffa_status ffa_search(const ffa_plan* plan, const void* d_series, void* d_workspace,
+                      size_t workspace_bytes, ffa_record* d_records, int32_t* d_status,
+                      void* stream);
+
+/* Candidate extraction (the first step of ffa2best, Section 2.3.3): records
+ * with S/N >= snr_min, highest first (ties: lower periodogram index first),
+ * at most top_k (<= 4096) of them, written to host memory `out`; *n_out
+ * receives the count and *best the globally best record's index (-1 if the
+ * periodogram is empty).  Uses the plan's workspace after the records;
+ * enqueues device kernels on `stream`, then waits for it with a bounded
+ * wait of timeout_ms (FFA_ERR_TIMEOUT on expiry) and copies the result. */
+ffa_status ffa_candidates(const ffa_plan* plan, const ffa_record* d_records, double snr_min,
+                          int32_t top_k, void* d_workspace, size_t workspace_bytes,
+                          ffa_candidate* out, int32_t* n_out, int64_t* best,
+                          int32_t* d_status, void* stream, int32_t timeout_ms);
+
+/* Wait for `stream` with a bounded wait (polling), then read *d_status.
+ * Returns FFA_ERR_TIMEOUT, FFA_ERR_CUDA, the device status, or FFA_OK. */
+ffa_status ffa_wait(void* stream, const int32_t* d_status, int32_t timeout_ms);
+
+/* ---- individual steps (for step-level parity checks) ----------------------- */
+
+/* Pre-/octave downsampling (Section 2.3): d_out[i] = sum_{j<factor}
+ * d_in[factor*i + j] in FP64 for i < n / factor (odd tail dropped). */
+ffa_status ffa_downsample(const void* d_in, int32_t in_type, int64_t n, int64_t factor,
+                          double* d_out, void* stream);
+
+/* Dynamic dereddening (Section 2.3): d_resid[i] = d_raw[i] - median of the
+ * centred window of `window` (odd) samples truncated at the series ends;
+ * an even count takes the mean of its two middle values.  Exact. */
+ffa_status ffa_detrend(const double* d_raw, int64_t n, int32_t window, double* d_resid,
+                       int32_t* d_status, void* stream);
+
+/* Normalisation: z = (r - mean) / std with the FP64 mean and population
+ * standard deviation of d_resid; writes float z (precision F32) or the int8
+ * code (precision I8) to d_out, and {mean, std} to d_stats[0..1].  d_stats
+ * must hold FFA_STATS_DOUBLES doubles (the rest is reduction scratch). */
+#define FFA_STATS_DOUBLES 1026
+ffa_status ffa_normalise(const double* d_resid, int64_t n, int32_t precision, void* d_out,
+                         double* d_stats, void* stream);
+
+/* The FFA of one base period (Section 2.1): d_z holds >= m_data * p0 samples
+ * (float for F32, int8 for I8); rows r >= m_data are zero; m_rows is a power
+ * of two >= m_data.  Writes the m_rows folded trials (float or int32) to
+ * d_plane (m_rows * p0 elements).  d_tmp: same size, scratch. */
+ffa_status ffa_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
+                    int64_t m_rows, void* d_plane, void* d_tmp, void* stream);
+
+/* Algorithm 1 (Section 2.2.1) on `count` profiles of p0 bins (float or
+ * int32 per precision), widths given on the host; one record per profile. */
+ffa_status ffa_score(const void* d_profiles, int32_t precision, int64_t count, int64_t p0,
+                     const int32_t* widths, int32_t n_widths, ffa_record* d_records,
+                     int32_t* d_status, void* stream);
+
+/* ---- timing (benchmark instrumentation) ---------------------------------------- */
+
+/* When enabled (process-wide), ffa_search records CUDA events on its stream
+ * around two phases of every octave: 0 = series preparation (downsampling,
+ * dereddening, normalisation) and 1 = fold + score of all base periods.
+ * ffa_timing_read waits for the recorded events, writes the summed
+ * milliseconds of phase p, octave o to ms[p * 64 + o] (cap >= 128 doubles)
+ * and the number of recorded intervals to counts[p * 64 + o], then clears
+ * the record.  Adds two event records per phase and octave; off by default. */
+ffa_status ffa_timing_enable(int32_t on);
+
+/* Number of kernel launches (and device copies) the library has enqueued in
+ * this process so far, all devices and threads together. */
+int64_t ffa_launch_count(void);
+ffa_status ffa_timing_read(double* ms, int32_t* counts, int32_t cap);
+
+/* ---- errors ------------------------------------------------------------------ */
+const char* ffa_status_string(ffa_status s);
+const char* ffa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFA_GB300_H */

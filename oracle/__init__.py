@@ -120,6 +120,7 @@ def lib():
             L.oracle_plan.restype = i64
             L.oracle_octave_series.argtypes = [P, P, i64, C.c_int, P, P, P, P, C.c_int]
             L.oracle_octave_series.restype = C.c_int
+            L.oracle_fold_score_rows.argtypes = [C.c_int, P, P, P, i64, P, C.c_int]
             L.oracle_search.argtypes = [P, P, i64, C.c_int, P, i64, C.c_int]
             L.oracle_search.restype = C.c_int
             L.oracle_best.argtypes = [P, i64]
@@ -254,6 +255,22 @@ def search(cfg: Config, series: np.ndarray, nthreads: int = 0) -> np.ndarray:
     if rc != 0:
         raise RuntimeError(f"oracle_search failed: {rc}")
     return rec[:nt]
+
+
+def fold_score_rows(fold_type: int, octaves: list, rows: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    """Fold and score the given plan rows; ``octaves`` = octave_series(...) output.
+
+    Returns one SCORE_DTYPE record per trial of the rows, in row order."""
+    buf = np.concatenate(octaves) if octaves else np.zeros(1)
+    offs = np.zeros(64, np.int64)
+    offs[1:len(octaves) + 1] = np.cumsum([o.size for o in octaves])
+    sub = np.ascontiguousarray(rows.copy())
+    sub["first_trial"] = np.concatenate([[0], np.cumsum(sub["m_rows"][:-1].astype(np.int64))])
+    total = int(sub["m_rows"].astype(np.int64).sum())
+    rec = np.zeros(max(total, 1), SCORE_DTYPE)
+    lib().oracle_fold_score_rows(int(fold_type), _p(buf), _p(offs), _p(sub), len(sub), _p(rec),
+                                 int(nthreads))
+    return rec[:total]
 
 
 def best(records: np.ndarray) -> int:

@@ -511,6 +511,52 @@ int oracle_octave_series(const oracle_cfg* cfg, const void* series, int64_t n, i
     return o;
 }
 
+// Fold and score the listed base periods (the inner loop of the search):
+// z holds every octave's series (offsets[o] = start of octave o) as FP64
+// (fold_type 0), FP32 (1) or int8 (2); records receive each row's trials at
+// row.first_trial.  Base periods run in parallel over `nthreads` threads.
+void oracle_fold_score_rows(int fold_type, const void* z, const int64_t* offsets,
+                            const oracle_plan_row* plan, int64_t np, oracle_score* records,
+                            int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t t = 0; t < np; ++t) {
+        const oracle_plan_row& r = plan[t];
+        int64_t p0 = r.p0, m = r.m_rows, md = r.m_data;
+        int64_t off = offsets[r.octave];
+        if (fold_type == 0) {
+            auto rows = make_rows((const double*)z + off, p0, md, m);
+            std::vector<double> out((size_t)(m * p0));
+            oracle_fold_f64(rows.data(), m, p0, out.data());
+            for (int64_t k = 0; k < m; ++k)
+                oracle_score_alg1_f64(out.data() + k * p0, p0, r.widths, r.n_widths,
+                                      &records[r.first_trial + k]);
+        } else if (fold_type == 1) {
+            auto rows = make_rows((const float*)z + off, p0, md, m);
+            std::vector<float> out((size_t)(m * p0));
+            oracle_fold_f32(rows.data(), m, p0, out.data());
+            std::vector<double> prof((size_t)p0);
+            for (int64_t k = 0; k < m; ++k) {
+                for (int64_t j = 0; j < p0; ++j) prof[j] = out[k * p0 + j];
+                oracle_score_alg1_f64(prof.data(), p0, r.widths, r.n_widths,
+                                      &records[r.first_trial + k]);
+            }
+        } else {
+            const int8_t* qz8 = (const int8_t*)z + off;
+            std::vector<int64_t> qz((size_t)(md * p0));
+            for (int64_t i = 0; i < md * p0; ++i) qz[i] = qz8[i];
+            auto rows = make_rows(qz.data(), p0, md, m);
+            std::vector<int64_t> out((size_t)(m * p0));
+            oracle_fold_i64(rows.data(), m, p0, out.data());
+            for (int64_t k = 0; k < m; ++k)
+                oracle_score_alg1_i64(out.data() + k * p0, p0, r.widths, r.n_widths,
+                                      &records[r.first_trial + k]);
+        }
+    }
+}
+
 // --- the whole search --------------------------------------------------------
 // series: n samples (in_type 0: float32, 1: uint8).  records: one per trial,
 // in (octave, P0, trial) order.  Base periods are folded in parallel over
@@ -543,42 +589,9 @@ int oracle_search(const oracle_cfg* cfg, const void* series, int64_t n, int in_t
     oracle_octave_series(cfg, series, n, in_type, z64.empty() ? nullptr : z64.data(),
                          z32.empty() ? nullptr : z32.data(), q.empty() ? nullptr : q.data(),
                          offsets.data(), 63);
-#ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1)
-#endif
-    for (int64_t t = 0; t < np; ++t) {
-        const oracle_plan_row& r = plan[(size_t)t];
-        int64_t p0 = r.p0, m = r.m_rows, md = r.m_data;
-        int64_t off = offsets[r.octave];
-        if (cfg->fold_type == 0) {
-            auto rows = make_rows(z64.data() + off, p0, md, m);
-            std::vector<double> out((size_t)(m * p0));
-            oracle_fold_f64(rows.data(), m, p0, out.data());
-            for (int64_t k = 0; k < m; ++k)
-                oracle_score_alg1_f64(out.data() + k * p0, p0, r.widths, r.n_widths,
-                                      &records[r.first_trial + k]);
-        } else if (cfg->fold_type == 1) {
-            auto rows = make_rows(z32.data() + off, p0, md, m);
-            std::vector<float> out((size_t)(m * p0));
-            oracle_fold_f32(rows.data(), m, p0, out.data());
-            std::vector<double> prof((size_t)p0);
-            for (int64_t k = 0; k < m; ++k) {
-                for (int64_t j = 0; j < p0; ++j) prof[j] = out[k * p0 + j];
-                oracle_score_alg1_f64(prof.data(), p0, r.widths, r.n_widths,
-                                      &records[r.first_trial + k]);
-            }
-        } else {
-            std::vector<int64_t> qz((size_t)(md * p0));
-            for (int64_t i = 0; i < md * p0; ++i) qz[i] = q[off + i];
-            auto rows = make_rows(qz.data(), p0, md, m);
-            std::vector<int64_t> out((size_t)(m * p0));
-            oracle_fold_i64(rows.data(), m, p0, out.data());
-            for (int64_t k = 0; k < m; ++k)
-                oracle_score_alg1_i64(out.data() + k * p0, p0, r.widths, r.n_widths,
-                                      &records[r.first_trial + k]);
-        }
-    }
+    const void* zs = cfg->fold_type == 0 ? (const void*)z64.data()
+                   : cfg->fold_type == 1 ? (const void*)z32.data() : (const void*)q.data();
+    oracle_fold_score_rows(cfg->fold_type, zs, offsets.data(), plan.data(), np, records, nthreads);
     return 0;
 }
 

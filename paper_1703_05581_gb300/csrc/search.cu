@@ -1,0 +1,664 @@
+// Host driver and C ABI of the FFA search: the plan (Section 2.1 padding,
+// Section 2.3 octaves and dereddening window), the search pipeline and the
+// candidate extraction (first step of ffa2best, Section 2.3.3).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+struct ffa_plan {
+    ffa_search_config cfg;
+    int64_t n = 0;       // input samples
+    int64_t n0 = 0;      // after pre-downsampling
+    int32_t window = 1;  // odd running-median window (1 = off)
+    int32_t n_octaves = 0;
+    int64_t n_trials = 0;
+    int64_t max_plane = 0;  // largest m_rows * p0
+    std::vector<ffa_plan_entry> entries;
+    std::vector<int64_t> oct_first, oct_count, oct_n;
+    // workspace layout (bytes)
+    size_t off_raw_a = 0, off_raw_b = 0, off_resid = 0, off_z = 0, off_stats = 0, off_plane0 = 0,
+           off_plane1 = 0, off_cand = 0, ws_bytes = 0;
+};
+
+namespace ffa {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string& msg) { g_err = msg; }
+ffa_status fail(ffa_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+ffa_status cuda_fail(cudaError_t e, const char* where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return FFA_ERR_CUDA;
+}
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+ffa_status ensure_smem(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> done;
+    int dev = 0;
+    FFA_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(func, dev);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return FFA_OK;
+    FFA_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done[key] = bytes;
+    return FFA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// candidate extraction kernels
+// ---------------------------------------------------------------------------
+struct CandCtl {
+    unsigned long long best_key;
+    uint32_t count;  // records with snr >= snr_min
+    uint32_t n_out;
+    unsigned long long prefix, mask;
+    uint32_t rank;
+    uint32_t take;   // min(top_k, count)
+    uint32_t hist[256];
+};
+
+struct CandOut {
+    int64_t trial;
+    float snr;
+    int32_t width;
+    int32_t phase;
+    int32_t pad;
+};
+
+constexpr int CAND_MAX = 4096;
+
+// ascending key = descending snr, then ascending trial index
+__device__ __forceinline__ unsigned long long cand_key(float snr, int64_t idx) {
+    return ((unsigned long long)(0xffffffffu - fkey(snr)) << 32) | (unsigned long long)(uint32_t)idx;
+}
+
+__global__ void k_cand_init(CandCtl* ctl) {
+    int t = threadIdx.x;
+    if (t == 0) {
+        ctl->best_key = ~0ull;
+        ctl->count = 0;
+        ctl->n_out = 0;
+        ctl->prefix = 0;
+        ctl->mask = 0;
+        ctl->rank = 0;
+        ctl->take = 0;
+    }
+    for (int b = t; b < 256; b += blockDim.x) ctl->hist[b] = 0;
+}
+
+__global__ void k_cand_count(const ffa_record* __restrict__ rec, int64_t n, float snr_min,
+                             CandCtl* ctl) {
+    __shared__ unsigned long long s_best;
+    __shared__ uint32_t s_cnt;
+    if (threadIdx.x == 0) {
+        s_best = ~0ull;
+        s_cnt = 0;
+    }
+    __syncthreads();
+    unsigned long long best = ~0ull;
+    uint32_t cnt = 0;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float s = rec[i].snr;
+        unsigned long long k = cand_key(s, i);
+        best = k < best ? k : best;
+        cnt += (s >= snr_min);
+    }
+    atomicMin(&s_best, best);
+    atomicAdd(&s_cnt, cnt);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicMin(&ctl->best_key, s_best);
+        atomicAdd(&ctl->count, s_cnt);
+    }
+}
+
+__global__ void k_cand_hist(const ffa_record* __restrict__ rec, int64_t n, float snr_min,
+                            int pass, CandCtl* ctl) {
+    __shared__ uint32_t h[256];
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const unsigned long long prefix = ctl->prefix, mask = ctl->mask;
+    const int shift = 56 - 8 * pass;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float s = rec[i].snr;
+        if (!(s >= snr_min)) continue;
+        unsigned long long k = cand_key(s, i);
+        if ((k & mask) == prefix) atomicAdd(&h[(k >> shift) & 0xff], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += blockDim.x)
+        if (h[b]) atomicAdd(&ctl->hist[b], h[b]);
+}
+
+__global__ void k_cand_pick(int pass, int top_k, CandCtl* ctl) {
+    if (threadIdx.x != 0) return;
+    if (pass == 0) {
+        ctl->take = ctl->count < (uint32_t)top_k ? ctl->count : (uint32_t)top_k;
+        ctl->rank = ctl->take > 0 ? ctl->take - 1 : 0;
+    }
+    if (ctl->take == 0) return;
+    const int shift = 56 - 8 * pass;
+    uint32_t c = 0;
+    for (int b = 0; b < 256; ++b) {
+        uint32_t h = ctl->hist[b];
+        if (ctl->rank < c + h) {
+            ctl->rank -= c;
+            ctl->prefix |= (unsigned long long)b << shift;
+            ctl->mask |= 0xffull << shift;
+            break;
+        }
+        c += h;
+    }
+    for (int b = 0; b < 256; ++b) ctl->hist[b] = 0;
+}
+
+__global__ void k_cand_compact(const ffa_record* __restrict__ rec, int64_t n, float snr_min,
+                               CandCtl* ctl, unsigned long long* keys) {
+    if (ctl->take == 0) return;
+    const unsigned long long thr = ctl->prefix;  // key of the take-th best
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float s = rec[i].snr;
+        if (!(s >= snr_min)) continue;
+        unsigned long long k = cand_key(s, i);
+        if (k <= thr) {
+            uint32_t slot = atomicAdd(&ctl->n_out, 1u);
+            if (slot < CAND_MAX) keys[slot] = k;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_cand_sort(const ffa_record* __restrict__ rec,
+                                                    CandCtl* ctl, const unsigned long long* keys,
+                                                    CandOut* out) {
+    __shared__ unsigned long long sk[CAND_MAX];
+    uint32_t n = ctl->n_out < CAND_MAX ? ctl->n_out : CAND_MAX;
+    uint32_t np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    for (uint32_t t = threadIdx.x; t < np2; t += blockDim.x) sk[t] = t < n ? keys[t] : ~0ull;
+    __syncthreads();
+    for (uint32_t kk = 2; kk <= np2; kk <<= 1) {
+        for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (uint32_t t = threadIdx.x; t < np2; t += blockDim.x) {
+                uint32_t u = t ^ jj;
+                if (u > t) {
+                    bool up = (t & kk) == 0;
+                    unsigned long long a = sk[t], b = sk[u];
+                    if ((a > b) == up) {
+                        sk[t] = b;
+                        sk[u] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+        int64_t idx = (int64_t)(uint32_t)(sk[t] & 0xffffffffull);
+        ffa_record r = rec[idx];
+        CandOut o;
+        o.trial = idx;
+        o.snr = r.snr;
+        o.width = r.width;
+        o.phase = r.phase;
+        o.pad = 0;
+        out[t] = o;
+    }
+}
+
+}  // namespace ffa
+
+using namespace ffa;
+
+namespace {
+// benchmark instrumentation: event pairs around (phase, octave) intervals
+struct TimingRec {
+    int phase, octave;
+    cudaEvent_t a, b;
+};
+std::mutex g_tmu;
+bool g_timing = false;
+std::vector<TimingRec> g_trec;
+
+struct PhaseTimer {
+    bool on = false;
+    TimingRec r;
+    cudaStream_t st;
+    PhaseTimer(int phase, int octave, cudaStream_t s) : st(s) {
+        {
+            std::lock_guard<std::mutex> lk(g_tmu);
+            on = g_timing;
+        }
+        if (!on) return;
+        r.phase = phase;
+        r.octave = octave;
+        if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+            on = false;
+            return;
+        }
+        cudaEventRecord(r.a, st);
+    }
+    void stop() {
+        if (!on) return;
+        cudaEventRecord(r.b, st);
+        std::lock_guard<std::mutex> lk(g_tmu);
+        g_trec.push_back(r);
+        on = false;
+    }
+};
+}  // namespace
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" {
+
+const char* ffa_status_string(ffa_status s) {
+    switch (s) {
+        case FFA_OK: return "ok";
+        case FFA_ERR_ARG: return "invalid argument";
+        case FFA_ERR_CUDA: return "CUDA error";
+        case FFA_ERR_OOM: return "buffer too small";
+        case FFA_ERR_TIMEOUT: return "timeout";
+        case FFA_ERR_CANCELLED: return "cancelled";
+        case FFA_ERR_UNSUPPORTED: return "unsupported";
+        case FFA_ERR_DEVICE: return "device-side check failed";
+    }
+    return "unknown status";
+}
+
+const char* ffa_last_error(void) { return ffa::g_err.c_str(); }
+
+ffa_status ffa_plan_create(const ffa_search_config* cfg, int64_t n, ffa_plan** out) {
+    if (!cfg || !out) return fail(FFA_ERR_ARG, "plan: null argument");
+    *out = nullptr;
+    if (!(cfg->tsamp_s > 0.0) || !(cfg->period_min_s > 0.0) ||
+        !(cfg->period_max_s > cfg->period_min_s))
+        return fail(FFA_ERR_ARG, "plan: need tsamp > 0 and 0 < period_min < period_max");
+    if (cfg->downsample0 < 1) return fail(FFA_ERR_ARG, "plan: downsample0 must be >= 1");
+    if (n < 0) return fail(FFA_ERR_ARG, "plan: negative length");
+    if (cfg->in_type != FFA_IN_F32 && cfg->in_type != FFA_IN_U8)
+        return fail(FFA_ERR_ARG, "plan: in_type must be FFA_IN_F32 or FFA_IN_U8");
+    if (cfg->precision != FFA_FOLD_F32 && cfg->precision != FFA_FOLD_I8)
+        return fail(FFA_ERR_ARG, "plan: bad precision");
+    if (cfg->n_widths_fixed < 0 || cfg->n_widths_fixed > 16)
+        return fail(FFA_ERR_ARG, "plan: n_widths_fixed must be in [0, 16]");
+    if (cfg->n_widths_fixed == 0 && !(cfg->duty_max > 0.0))
+        return fail(FFA_ERR_ARG, "plan: duty_max must be > 0 without fixed widths");
+    for (int t = 0; t < cfg->n_widths_fixed; ++t) {
+        int32_t w = cfg->widths_fixed[t];
+        if (w < 1 || (w & (w - 1)) != 0 || (t > 0 && w <= cfg->widths_fixed[t - 1]))
+            return fail(FFA_ERR_UNSUPPORTED, "plan: widths must be increasing powers of two");
+    }
+    ffa_plan* p = new (std::nothrow) ffa_plan();
+    if (!p) return fail(FFA_ERR_OOM, "plan: host allocation failed");
+    p->cfg = *cfg;
+    p->n = n;
+    const int64_t d0 = cfg->downsample0;
+    p->n0 = n / d0;
+    const double pmin = cfg->period_min_s / (cfg->tsamp_s * (double)d0);
+    const double pmax = cfg->period_max_s / (cfg->tsamp_s * (double)d0);
+    int64_t p_min = (int64_t)std::ceil(pmin - 1e-9);
+    if (p_min < 1) p_min = 1;
+    const int64_t p_max = (int64_t)std::ceil(pmax - 1e-9);
+    int64_t w = cfg->detrend_window > 0 ? cfg->detrend_window : std::min(2 * p_max, 4 * p_min);
+    if (cfg->detrend_window < 0) w = 1;
+    w |= 1;
+    if (w > INT32_MAX) w = INT32_MAX;
+    p->window = (int32_t)w;
+    const int64_t min_rows = cfg->min_rows > 0 ? cfg->min_rows : 2;
+    int64_t n_o = p->n0;
+    for (int32_t o = 0; o < 62; ++o) {
+        if (o > 0) n_o /= 2;
+        int64_t hi = std::min<int64_t>(2 * p_min, (int64_t)std::ceil(pmax / std::ldexp(1.0, o) - 1e-9));
+        if (hi <= p_min || n_o <= 0) break;
+        int64_t first = (int64_t)p->entries.size();
+        for (int64_t p0 = p_min; p0 < hi; ++p0) {
+            int64_t m_data = n_o / p0;
+            if (m_data < min_rows) continue;
+            int64_t m = 1;
+            while (m < m_data) m *= 2;
+            ffa_plan_entry e;
+            std::memset(&e, 0, sizeof(e));
+            e.octave = o;
+            e.p0 = (int32_t)p0;
+            e.m_data = (int32_t)m_data;
+            e.m_rows = (int32_t)m;
+            e.n_octave = n_o;
+            e.first_trial = p->n_trials;
+            if (cfg->n_widths_fixed > 0) {
+                e.n_widths = cfg->n_widths_fixed;
+                for (int t = 0; t < e.n_widths; ++t) e.widths[t] = cfg->widths_fixed[t];
+            } else {
+                int nw = 0;
+                for (int64_t wd = 1;; wd *= 2) {
+                    e.widths[nw++] = (int32_t)wd;
+                    if ((double)wd > cfg->duty_max * (double)p0 || nw == 16) break;
+                }
+                e.n_widths = nw;
+            }
+            if (p0 > 32768) {
+                delete p;
+                return fail(FFA_ERR_UNSUPPORTED,
+                            "plan: base periods above 32768 bins; raise downsample0");
+            }
+            if (cfg->precision == FFA_FOLD_I8) {
+                // int32 box sums: |box| <= 127 * m_data * widest box
+                double bound = 127.0 * (double)m_data * (double)e.widths[e.n_widths - 1];
+                if (bound >= 2147483647.0) {
+                    delete p;
+                    return fail(FFA_ERR_UNSUPPORTED, "plan: int8 path would overflow int32 box sums");
+                }
+            }
+            p->entries.push_back(e);
+            p->n_trials += m;
+            p->max_plane = std::max<int64_t>(p->max_plane, m * p0);
+        }
+        int64_t cnt = (int64_t)p->entries.size() - first;
+        if (cnt > 0) {
+            p->oct_first.push_back(first);
+            p->oct_count.push_back(cnt);
+            p->oct_n.push_back(n_o);
+            p->n_octaves = o + 1;
+        } else {
+            break;  // fewer rows at every later octave
+        }
+    }
+    if (p->n_trials >= (int64_t)1 << 32) {
+        delete p;
+        return fail(FFA_ERR_UNSUPPORTED, "plan: more than 2^32 trials");
+    }
+    // workspace layout
+    const int64_t n0 = std::max<int64_t>(p->n0, 1);
+    size_t off = 0;
+    p->off_raw_a = off;
+    off = align256(off + sizeof(double) * n0);
+    p->off_raw_b = off;
+    off = align256(off + sizeof(double) * (n0 / 2 + 1));
+    p->off_resid = off;
+    off = align256(off + sizeof(double) * n0);
+    p->off_z = off;
+    off = align256(off + (cfg->precision == FFA_FOLD_F32 ? 4 : 1) * (size_t)n0);
+    p->off_stats = off;
+    off = align256(off + sizeof(double) * STATS_DOUBLES);
+    p->off_plane0 = off;
+    off = align256(off + 4 * (size_t)std::max<int64_t>(p->max_plane, 1));
+    p->off_plane1 = off;
+    off = align256(off + 4 * (size_t)std::max<int64_t>(p->max_plane, 1));
+    p->off_cand = off;
+    off = align256(off + sizeof(CandCtl) + 256 + sizeof(unsigned long long) * CAND_MAX +
+                   sizeof(CandOut) * CAND_MAX);
+    p->ws_bytes = off;
+    *out = p;
+    return FFA_OK;
+}
+
+void ffa_plan_destroy(ffa_plan* plan) { delete plan; }
+
+ffa_status ffa_plan_info(const ffa_plan* p, int64_t* n_periods, int64_t* n_trials,
+                         int32_t* n_octaves, int32_t* window, size_t* workspace_bytes) {
+    if (!p) return fail(FFA_ERR_ARG, "plan_info: null plan");
+    if (n_periods) *n_periods = (int64_t)p->entries.size();
+    if (n_trials) *n_trials = p->n_trials;
+    if (n_octaves) *n_octaves = p->n_octaves;
+    if (window) *window = p->window;
+    if (workspace_bytes) *workspace_bytes = p->ws_bytes;
+    return FFA_OK;
+}
+
+ffa_status ffa_plan_entries(const ffa_plan* p, ffa_plan_entry* out, int64_t cap) {
+    if (!p || (!out && cap > 0)) return fail(FFA_ERR_ARG, "plan_entries: null argument");
+    int64_t m = std::min<int64_t>(cap, (int64_t)p->entries.size());
+    if (m > 0) std::memcpy(out, p->entries.data(), sizeof(ffa_plan_entry) * (size_t)m);
+    return FFA_OK;
+}
+
+ffa_status ffa_search(const ffa_plan* p, const void* d_series, void* d_ws, size_t ws_bytes,
+                      ffa_record* d_records, int32_t* d_status, void* stream) {
+    if (!p) return fail(FFA_ERR_ARG, "search: null plan");
+    if (p->n_trials == 0) return FFA_OK;
+    if (!d_series || !d_ws || !d_records) return fail(FFA_ERR_ARG, "search: null buffer");
+    if (ws_bytes < p->ws_bytes) return fail(FFA_ERR_OOM, "search: workspace too small");
+    if ((uintptr_t)d_ws % 256 != 0) return fail(FFA_ERR_ARG, "search: workspace not 256-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    char* ws = (char*)d_ws;
+    double* raw[2] = {(double*)(ws + p->off_raw_a), (double*)(ws + p->off_raw_b)};
+    double* resid = (double*)(ws + p->off_resid);
+    void* z = ws + p->off_z;
+    double* stats = (double*)(ws + p->off_stats);
+    void* plane0 = ws + p->off_plane0;
+    void* plane1 = ws + p->off_plane1;
+    const ffa_search_config& c = p->cfg;
+    ffa_status s = launch_downsample(d_series, c.in_type, p->n, c.downsample0, raw[0], st);
+    if (s != FFA_OK) return s;
+    int64_t n_o = p->n0;
+    for (int32_t o = 0; o < p->n_octaves; ++o) {
+        PhaseTimer prep_t(0, o, st);
+        double* cur = raw[o & 1];
+        if (o > 0) {
+            s = launch_downsample(raw[(o - 1) & 1], FFA_IN_F64, n_o, 2, cur, st);
+            if (s != FFA_OK) return s;
+            n_o /= 2;
+        }
+        if (p->window > 1) {
+            s = launch_detrend(cur, n_o, p->window, resid, d_status, st);
+        } else {
+            cudaError_t e = cudaMemcpyAsync(resid, cur, sizeof(double) * n_o, cudaMemcpyDeviceToDevice, st);
+            count_launch();
+            s = e == cudaSuccess ? FFA_OK : cuda_fail(e, "search: copy");
+        }
+        if (s != FFA_OK) return s;
+        s = launch_normalise(resid, n_o, c.precision, z, stats, st);
+        if (s != FFA_OK) return s;
+        prep_t.stop();
+        PhaseTimer fold_t(1, o, st);
+        for (int64_t t = 0; t < p->oct_count[o]; ++t) {
+            const ffa_plan_entry& e = p->entries[(size_t)(p->oct_first[o] + t)];
+            s = launch_fold(z, c.precision, e.p0, e.m_data, e.m_rows, plane0, plane1, st);
+            if (s != FFA_OK) return s;
+            ScoreWidths wd;
+            wd.n = e.n_widths;
+            for (int k = 0; k < 16; ++k) wd.w[k] = e.widths[k];
+            s = launch_score(plane0, c.precision, e.m_rows, e.p0, wd, d_records + e.first_trial,
+                             d_status, st);
+            if (s != FFA_OK) return s;
+        }
+        fold_t.stop();
+    }
+    return FFA_OK;
+}
+
+int64_t ffa_launch_count(void) { return (int64_t)ffa::g_launches.load(); }
+
+ffa_status ffa_timing_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_timing = on != 0;
+    return FFA_OK;
+}
+
+ffa_status ffa_timing_read(double* ms, int32_t* counts, int32_t cap) {
+    if (!ms || !counts || cap < 128) return fail(FFA_ERR_ARG, "timing_read: need cap >= 128");
+    std::vector<TimingRec> recs;
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        recs.swap(g_trec);
+    }
+    for (int i = 0; i < cap; ++i) {
+        ms[i] = 0.0;
+        counts[i] = 0;
+    }
+    ffa_status st = FFA_OK;
+    for (auto& r : recs) {
+        float t = 0.0f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) st = cuda_fail(e, "timing_read");
+        int idx = r.phase * 64 + (r.octave < 64 ? r.octave : 63);
+        if (idx < cap) {
+            ms[idx] += t;
+            counts[idx] += 1;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    return st;
+}
+
+ffa_status ffa_wait(void* stream, const int32_t* d_status, int32_t timeout_ms) {
+    cudaStream_t st = as_stream(stream);
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "wait: cudaStreamQuery");
+        auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                      std::chrono::steady_clock::now() - t0).count();
+        if (timeout_ms >= 0 && ms > timeout_ms) return fail(FFA_ERR_TIMEOUT, "wait: stream did not finish in time");
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    if (d_status) {
+        int32_t h = 0;
+        FFA_CUDA_TRY(cudaMemcpy(&h, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (h != 0) return fail((ffa_status)h, "device-side check failed");
+    }
+    return FFA_OK;
+}
+
+ffa_status ffa_candidates(const ffa_plan* p, const ffa_record* d_records, double snr_min,
+                          int32_t top_k, void* d_ws, size_t ws_bytes, ffa_candidate* out,
+                          int32_t* n_out, int64_t* best, int32_t* d_status, void* stream,
+                          int32_t timeout_ms) {
+    if (!p || !n_out || !best) return fail(FFA_ERR_ARG, "candidates: null argument");
+    if (top_k < 0 || top_k > CAND_MAX) return fail(FFA_ERR_ARG, "candidates: top_k must be in [0, 4096]");
+    if (top_k > 0 && !out) return fail(FFA_ERR_ARG, "candidates: null output");
+    *n_out = 0;
+    *best = -1;
+    if (p->n_trials == 0) return FFA_OK;
+    if (!d_records || !d_ws) return fail(FFA_ERR_ARG, "candidates: null buffer");
+    if (ws_bytes < p->ws_bytes) return fail(FFA_ERR_OOM, "candidates: workspace too small");
+    cudaStream_t st = as_stream(stream);
+    char* base = (char*)d_ws + p->off_cand;
+    CandCtl* ctl = (CandCtl*)base;
+    unsigned long long* keys = (unsigned long long*)(base + align256(sizeof(CandCtl)));
+    CandOut* cout = (CandOut*)(base + align256(sizeof(CandCtl)) + sizeof(unsigned long long) * CAND_MAX);
+    const int64_t n = p->n_trials;
+    const float smin = (float)snr_min;
+    const int grid = 152 * 8;
+    k_cand_init<<<1, 256, 0, st>>>(ctl);
+    k_cand_count<<<grid, 256, 0, st>>>(d_records, n, smin, ctl);
+    for (int pass = 0; pass < 8; ++pass) {
+        k_cand_hist<<<grid, 256, 0, st>>>(d_records, n, smin, pass, ctl);
+        k_cand_pick<<<1, 32, 0, st>>>(pass, top_k, ctl);
+    }
+    k_cand_compact<<<grid, 256, 0, st>>>(d_records, n, smin, ctl, keys);
+    k_cand_sort<<<1, 1024, 0, st>>>(d_records, ctl, keys, cout);
+    FFA_LAUNCH_CHECK("candidates kernels");
+    count_launch(21);
+    ffa_status s = ffa_wait(stream, d_status, timeout_ms);
+    if (s != FFA_OK) return s;
+    CandCtl h;
+    FFA_CUDA_TRY(cudaMemcpy(&h, ctl, sizeof(CandCtl), cudaMemcpyDeviceToHost));
+    uint32_t m = std::min<uint32_t>(h.n_out, (uint32_t)top_k);
+    std::vector<CandOut> buf(m);
+    if (m > 0) FFA_CUDA_TRY(cudaMemcpy(buf.data(), cout, sizeof(CandOut) * m, cudaMemcpyDeviceToHost));
+    if (h.best_key != ~0ull) *best = (int64_t)(uint32_t)(h.best_key & 0xffffffffull);
+    const ffa_search_config& c = p->cfg;
+    for (uint32_t t = 0; t < m; ++t) {
+        const CandOut& o = buf[t];
+        // entry holding this trial: the last one with first_trial <= trial
+        auto it = std::upper_bound(p->entries.begin(), p->entries.end(), o.trial,
+                                   [](int64_t v, const ffa_plan_entry& e) { return v < e.first_trial; });
+        const ffa_plan_entry& e = *(it - 1);
+        ffa_candidate& d = out[t];
+        d.trial = o.trial;
+        d.octave = e.octave;
+        d.p0 = e.p0;
+        d.k = (int32_t)(o.trial - e.first_trial);
+        d.snr = o.snr;
+        d.width = o.width;
+        d.phase = o.phase;
+        double scale = c.tsamp_s * (double)c.downsample0 * std::ldexp(1.0, e.octave);
+        d.period_s = ((double)e.p0 + (double)d.k / (double)(e.m_rows - 1)) * scale;
+    }
+    *n_out = (int32_t)m;
+    return FFA_OK;
+}
+
+// ---- step entry points ------------------------------------------------------
+
+ffa_status ffa_downsample(const void* d_in, int32_t in_type, int64_t n, int64_t factor,
+                          double* d_out, void* stream) {
+    if (n < 0 || factor < 1) return fail(FFA_ERR_ARG, "downsample: need n >= 0 and factor >= 1");
+    if (n / factor > 0 && (!d_in || !d_out)) return fail(FFA_ERR_ARG, "downsample: null buffer");
+    return launch_downsample(d_in, in_type, n, factor, d_out, as_stream(stream));
+}
+
+ffa_status ffa_detrend(const double* d_raw, int64_t n, int32_t window, double* d_resid,
+                       int32_t* d_status, void* stream) {
+    if (n < 0 || window < 1) return fail(FFA_ERR_ARG, "detrend: need n >= 0 and window >= 1");
+    if (n > 0 && (!d_raw || !d_resid)) return fail(FFA_ERR_ARG, "detrend: null buffer");
+    if (n >= ((int64_t)1 << 31)) return fail(FFA_ERR_UNSUPPORTED, "detrend: n >= 2^31");
+    return launch_detrend(d_raw, n, window, d_resid, d_status, as_stream(stream));
+}
+
+ffa_status ffa_normalise(const double* d_resid, int64_t n, int32_t precision, void* d_out,
+                         double* d_stats, void* stream) {
+    if (n < 0) return fail(FFA_ERR_ARG, "normalise: negative length");
+    if (precision != FFA_FOLD_F32 && precision != FFA_FOLD_I8) return fail(FFA_ERR_ARG, "normalise: bad precision");
+    if (n > 0 && (!d_resid || !d_out || !d_stats)) return fail(FFA_ERR_ARG, "normalise: null buffer");
+    return launch_normalise(d_resid, n, precision, d_out, d_stats, as_stream(stream));
+}
+
+ffa_status ffa_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data, int64_t m_rows,
+                    void* d_plane, void* d_tmp, void* stream) {
+    if (p0 < 1 || m_data < 0 || m_rows < 1 || (m_rows & (m_rows - 1)) != 0 || m_data > m_rows)
+        return fail(FFA_ERR_ARG, "fold: need p0 >= 1, m_rows a power of two >= m_data");
+    if (precision != FFA_FOLD_F32 && precision != FFA_FOLD_I8) return fail(FFA_ERR_ARG, "fold: bad precision");
+    if (!d_z || !d_plane || !d_tmp) return fail(FFA_ERR_ARG, "fold: null buffer");
+    return launch_fold(d_z, precision, p0, m_data, m_rows, d_plane, d_tmp, as_stream(stream));
+}
+
+ffa_status ffa_score(const void* d_profiles, int32_t precision, int64_t count, int64_t p0,
+                     const int32_t* widths, int32_t n_widths, ffa_record* d_records,
+                     int32_t* d_status, void* stream) {
+    if (count < 0 || p0 < 1) return fail(FFA_ERR_ARG, "score: need count >= 0 and p0 >= 1");
+    if (n_widths < 1 || n_widths > 16 || !widths) return fail(FFA_ERR_ARG, "score: 1..16 widths");
+    ScoreWidths wd;
+    wd.n = n_widths;
+    for (int t = 0; t < 16; ++t) wd.w[t] = t < n_widths ? widths[t] : 0;
+    for (int t = 0; t < n_widths; ++t) {
+        int32_t w = widths[t];
+        if (w < 1 || (w & (w - 1)) != 0 || (t > 0 && w <= widths[t - 1]))
+            return fail(FFA_ERR_UNSUPPORTED, "score: widths must be increasing powers of two");
+    }
+    if (count > 0 && (!d_profiles || !d_records)) return fail(FFA_ERR_ARG, "score: null buffer");
+    if (precision != FFA_FOLD_F32 && precision != FFA_FOLD_I8) return fail(FFA_ERR_ARG, "score: bad precision");
+    return launch_score(d_profiles, precision, count, p0, wd, d_records, d_status, as_stream(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,293 @@
+"""Thin Python binding of the C ABI in include/ffa.h (argument marshalling only).
+
+Every step of the search runs in the CUDA library libffa_gb300.so; PyTorch only
+provides device memory and streams.  Importing this module raises if the
+library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libffa_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1703_05581_gb300.build_lib.build()")
+
+_lib = C.CDLL(LIB_PATH)
+
+OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_CANCELLED, ERR_UNSUPPORTED, ERR_DEVICE = range(8)
+IN_F32, IN_U8, IN_F64 = 0, 1, 2
+FOLD_F32, FOLD_I8 = 0, 1
+STATS_DOUBLES = 1026
+
+
+class FFAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.ffa_status_string(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+class SearchConfig(C.Structure):
+    _fields_ = [("tsamp_s", C.c_double), ("period_min_s", C.c_double),
+                ("period_max_s", C.c_double), ("duty_max", C.c_double),
+                ("downsample0", C.c_int32), ("detrend_window", C.c_int32),
+                ("min_rows", C.c_int32), ("in_type", C.c_int32), ("precision", C.c_int32),
+                ("n_widths_fixed", C.c_int32), ("widths_fixed", C.c_int32 * 16)]
+
+
+class Record(C.Structure):
+    _fields_ = [("snr", C.c_float), ("width", C.c_int32), ("phase", C.c_int32),
+                ("flags", C.c_uint32)]
+
+
+class PlanEntry(C.Structure):
+    _fields_ = [("octave", C.c_int32), ("p0", C.c_int32), ("m_data", C.c_int32),
+                ("m_rows", C.c_int32), ("n_widths", C.c_int32), ("widths", C.c_int32 * 16),
+                ("pad", C.c_int32), ("n_octave", C.c_int64), ("first_trial", C.c_int64)]
+
+
+class Candidate(C.Structure):
+    _fields_ = [("trial", C.c_int64), ("period_s", C.c_double), ("snr", C.c_float),
+                ("octave", C.c_int32), ("p0", C.c_int32), ("k", C.c_int32),
+                ("width", C.c_int32), ("phase", C.c_int32)]
+
+
+RECORD_DTYPE = np.dtype([("snr", "<f4"), ("width", "<i4"), ("phase", "<i4"), ("flags", "<u4")])
+ENTRY_DTYPE = np.dtype([("octave", "<i4"), ("p0", "<i4"), ("m_data", "<i4"), ("m_rows", "<i4"),
+                        ("n_widths", "<i4"), ("widths", "<i4", (16,)), ("pad", "<i4"),
+                        ("n_octave", "<i8"), ("first_trial", "<i8")])
+CANDIDATE_DTYPE = np.dtype([("trial", "<i8"), ("period_s", "<f8"), ("snr", "<f4"),
+                            ("octave", "<i4"), ("p0", "<i4"), ("k", "<i4"), ("width", "<i4"),
+                            ("phase", "<i4")])
+assert C.sizeof(Record) == 16 and RECORD_DTYPE.itemsize == 16
+assert C.sizeof(PlanEntry) == ENTRY_DTYPE.itemsize
+assert C.sizeof(Candidate) == CANDIDATE_DTYPE.itemsize
+
+_P, _i64, _i32 = C.c_void_p, C.c_int64, C.c_int32
+_sig = {
+    "ffa_plan_create": ([C.POINTER(SearchConfig), _i64, C.POINTER(C.c_void_p)], C.c_int),
+    "ffa_plan_destroy": ([_P], None),
+    "ffa_plan_info": ([_P, _P, _P, _P, _P, _P], C.c_int),
+    "ffa_plan_entries": ([_P, _P, _i64], C.c_int),
+    "ffa_search": ([_P, _P, _P, C.c_size_t, _P, _P, _P], C.c_int),
+    "ffa_candidates": ([_P, _P, C.c_double, _i32, _P, C.c_size_t, _P, _P, _P, _P, _P, _i32],
+                       C.c_int),
+    "ffa_wait": ([_P, _P, _i32], C.c_int),
+    "ffa_downsample": ([_P, _i32, _i64, _i64, _P, _P], C.c_int),
+    "ffa_detrend": ([_P, _i64, _i32, _P, _P, _P], C.c_int),
+    "ffa_normalise": ([_P, _i64, _i32, _P, _P, _P], C.c_int),
+    "ffa_fold": ([_P, _i32, _i64, _i64, _i64, _P, _P, _P], C.c_int),
+    "ffa_score": ([_P, _i32, _i64, _i64, _P, _i32, _P, _P, _P], C.c_int),
+    "ffa_timing_enable": ([_i32], C.c_int),
+    "ffa_launch_count": ([], C.c_int64),
+    "ffa_timing_read": ([_P, _P, _i32], C.c_int),
+    "ffa_status_string": ([C.c_int], C.c_char_p),
+    "ffa_last_error": ([], C.c_char_p),
+}
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTS = tuple(_sig)
+
+
+def _check(status: int) -> None:
+    if status != OK:
+        raise FFAError(status, _lib.ffa_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class Config:
+    """Search configuration (periods in seconds), mirrors ffa_search_config."""
+
+    tsamp: float
+    period_min: float
+    period_max: float
+    duty: float = 0.2
+    downsample0: int = 1
+    detrend_window: int = 0
+    min_rows: int = 2
+    in_type: int = IN_F32
+    precision: int = FOLD_F32
+    widths: tuple = field(default_factory=tuple)
+
+    def c(self) -> SearchConfig:
+        c = SearchConfig()
+        c.tsamp_s, c.period_min_s, c.period_max_s, c.duty_max = (
+            self.tsamp, self.period_min, self.period_max, self.duty)
+        c.downsample0, c.detrend_window, c.min_rows = (self.downsample0, self.detrend_window,
+                                                       self.min_rows)
+        c.in_type, c.precision = self.in_type, self.precision
+        c.n_widths_fixed = len(self.widths)
+        for i, w in enumerate(self.widths):
+            c.widths_fixed[i] = int(w)
+        return c
+
+
+class Plan:
+    """ffa_plan for a series of n input samples."""
+
+    def __init__(self, cfg: Config, n: int):
+        self.cfg = cfg
+        self.n = int(n)
+        h = C.c_void_p()
+        self._c = cfg.c()
+        _check(_lib.ffa_plan_create(C.byref(self._c), self.n, C.byref(h)))
+        self._h = h
+        npd, nt, no = C.c_int64(), C.c_int64(), C.c_int32()
+        win, ws = C.c_int32(), C.c_size_t()
+        _check(_lib.ffa_plan_info(h, C.byref(npd), C.byref(nt), C.byref(no), C.byref(win),
+                                  C.byref(ws)))
+        self.n_periods, self.n_trials, self.n_octaves = npd.value, nt.value, no.value
+        self.window, self.workspace_bytes = win.value, ws.value
+        self.entries = np.zeros(self.n_periods, ENTRY_DTYPE)
+        if self.n_periods:
+            _check(_lib.ffa_plan_entries(h, self.entries.ctypes.data_as(C.c_void_p),
+                                         self.n_periods))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.ffa_plan_destroy(h)
+            self._h = None
+
+    def periods(self) -> np.ndarray:
+        out = []
+        for e in self.entries:
+            m = int(e["m_rows"])
+            scale = self.cfg.tsamp * self.cfg.downsample0 * 2.0 ** int(e["octave"])
+            out.append((e["p0"] + np.arange(m) / (m - 1)) * scale)
+        return np.concatenate(out) if out else np.zeros(0)
+
+    def workspace(self, device=None) -> torch.Tensor:
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        return torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=dev)
+
+    def records(self, device=None) -> torch.Tensor:
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        return torch.empty((max(self.n_trials, 1), 4), dtype=torch.int32, device=dev)
+
+
+def status_word(device=None) -> torch.Tensor:
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    return torch.zeros(1, dtype=torch.int32, device=dev)
+
+
+def search(plan: Plan, series: torch.Tensor, workspace: torch.Tensor | None = None,
+           records: torch.Tensor | None = None, status: torch.Tensor | None = None,
+           stream=None) -> torch.Tensor:
+    """Enqueue the whole search; returns the (n_trials, 4) int32 view of the records."""
+    assert series.is_cuda and series.is_contiguous() and series.numel() == plan.n
+    workspace = plan.workspace(series.device) if workspace is None else workspace
+    records = plan.records(series.device) if records is None else records
+    status = status_word(series.device) if status is None else status
+    _check(_lib.ffa_search(plan._h, _ptr(series), _ptr(workspace), workspace.numel(),
+                           _ptr(records), _ptr(status), _stream(stream)))
+    return records
+
+
+def records_numpy(records: torch.Tensor, n: int) -> np.ndarray:
+    return records[:n].cpu().numpy().view(RECORD_DTYPE).reshape(-1)
+
+
+def candidates(plan: Plan, records: torch.Tensor, workspace: torch.Tensor, snr_min: float,
+               top_k: int = 64, status: torch.Tensor | None = None, stream=None,
+               timeout_ms: int = 600000):
+    """Return (candidates structured array, best trial index)."""
+    status = status_word(records.device) if status is None else status
+    out = np.zeros(max(top_k, 1), CANDIDATE_DTYPE)
+    n_out, best = C.c_int32(), C.c_int64()
+    _check(_lib.ffa_candidates(plan._h, _ptr(records), float(snr_min), int(top_k),
+                               _ptr(workspace), workspace.numel(),
+                               out.ctypes.data_as(C.c_void_p), C.byref(n_out), C.byref(best),
+                               _ptr(status), _stream(stream), int(timeout_ms)))
+    return out[: n_out.value], best.value
+
+
+def wait(status: torch.Tensor | None = None, stream=None, timeout_ms: int = 600000) -> None:
+    _check(_lib.ffa_wait(_stream(stream), _ptr(status), int(timeout_ms)))
+
+
+def timing_enable(on: bool) -> None:
+    _check(_lib.ffa_timing_enable(1 if on else 0))
+
+
+def launch_count() -> int:
+    return int(_lib.ffa_launch_count())
+
+
+def timing_read():
+    """Return (ms[2, 64], counts[2, 64]) summed per (phase, octave); clears the record."""
+    ms = np.zeros(128, np.float64)
+    cnt = np.zeros(128, np.int32)
+    _check(_lib.ffa_timing_read(ms.ctypes.data_as(C.c_void_p), cnt.ctypes.data_as(C.c_void_p), 128))
+    return ms.reshape(2, 64), cnt.reshape(2, 64)
+
+
+# ---- individual steps --------------------------------------------------------
+
+_IN_TYPES = {torch.float32: IN_F32, torch.uint8: IN_U8, torch.float64: IN_F64}
+
+
+def downsample(x: torch.Tensor, factor: int, stream=None) -> torch.Tensor:
+    out = torch.empty(x.numel() // factor, dtype=torch.float64, device=x.device)
+    _check(_lib.ffa_downsample(_ptr(x), _IN_TYPES[x.dtype], x.numel(), int(factor), _ptr(out),
+                               _stream(stream)))
+    return out
+
+
+def detrend(raw: torch.Tensor, window: int, status: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+    assert raw.dtype == torch.float64
+    out = torch.empty_like(raw)
+    _check(_lib.ffa_detrend(_ptr(raw), raw.numel(), int(window), _ptr(out), _ptr(status),
+                            _stream(stream)))
+    return out
+
+
+def normalise(resid: torch.Tensor, precision: int = FOLD_F32, stream=None):
+    """Return (z or q, stats tensor whose first two entries are mean and std)."""
+    dt = torch.float32 if precision == FOLD_F32 else torch.int8
+    out = torch.empty(resid.numel(), dtype=dt, device=resid.device)
+    stats = torch.zeros(STATS_DOUBLES, dtype=torch.float64, device=resid.device)
+    _check(_lib.ffa_normalise(_ptr(resid), resid.numel(), precision, _ptr(out), _ptr(stats),
+                              _stream(stream)))
+    return out, stats
+
+
+def fold(z: torch.Tensor, p0: int, m_data: int, m_rows: int, stream=None) -> torch.Tensor:
+    prec = FOLD_F32 if z.dtype == torch.float32 else FOLD_I8
+    dt = torch.float32 if prec == FOLD_F32 else torch.int32
+    plane = torch.empty((m_rows, p0), dtype=dt, device=z.device)
+    tmp = torch.empty_like(plane)
+    _check(_lib.ffa_fold(_ptr(z), prec, int(p0), int(m_data), int(m_rows), _ptr(plane), _ptr(tmp),
+                         _stream(stream)))
+    return plane
+
+
+def score(profiles: torch.Tensor, widths, status: torch.Tensor | None = None,
+          stream=None) -> torch.Tensor:
+    prec = FOLD_F32 if profiles.dtype == torch.float32 else FOLD_I8
+    count, p0 = profiles.shape
+    w = np.ascontiguousarray(widths, np.int32)
+    rec = torch.empty((max(count, 1), 4), dtype=torch.int32, device=profiles.device)
+    _check(_lib.ffa_score(_ptr(profiles), prec, count, p0, w.ctypes.data_as(C.c_void_p), w.size,
+                          _ptr(rec), _ptr(status), _stream(stream)))
+    return rec

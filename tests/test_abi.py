@@ -1,0 +1,95 @@
+"""CPU checks of the C ABI: the library loads, exports every declared entry
+point, and its host-side planner agrees with the oracle's plan."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ffa():
+    from paper_1703_05581_gb300 import build_lib
+    build_lib.build()
+    from paper_1703_05581_gb300 import ffa as mod
+    return mod
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"^[A-Za-z_][\w \*]*?\b(ffa_\w+)\s*\(", txt, flags=re.M))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(ffa):
+    import ctypes
+    lib = ctypes.CDLL(ffa.LIB_PATH)
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(ffa.EXPORTS) | {"ffa_plan_destroy"}
+
+
+def test_status_strings(ffa):
+    for s in range(8):
+        assert ffa._lib.ffa_status_string(s)
+
+
+CONFIGS = [
+    (65536, dict(tsamp=2.048e-3, period_min=256 * 2.048e-3, period_max=512 * 2.048e-3,
+                 widths=(1, 2, 4, 8, 16))),
+    (1 << 26, dict(tsamp=64e-6, period_min=1.0, period_max=30.0, duty=0.1)),
+    (1 << 26, dict(tsamp=64e-6, period_min=1.0, period_max=30.0, duty=0.1, downsample0=64)),
+    ((1 << 22) + 12345, dict(tsamp=512e-6, period_min=0.5, period_max=20.0, duty=0.2)),
+    (5000, dict(tsamp=1e-3, period_min=0.1, period_max=0.35, duty=0.2, min_rows=4)),
+    (100, dict(tsamp=1e-3, period_min=0.2, period_max=0.4)),
+]
+
+
+@pytest.mark.parametrize("n,kw", CONFIGS)
+def test_planner_matches_oracle(ffa, orc, n, kw):
+    plan = ffa.Plan(ffa.Config(**kw), n)
+    rows, nt, w = orc.plan(orc.Config(**kw), n)
+    assert plan.n_trials == nt and plan.window == w and plan.n_periods == len(rows)
+    for k in ("octave", "p0", "m_data", "m_rows", "n_widths", "n_octave", "first_trial"):
+        assert np.array_equal(plan.entries[k], rows[k]), k
+    assert np.array_equal(plan.entries["widths"], rows["widths"])
+    if nt:
+        assert np.allclose(plan.periods(), orc.trial_periods(rows, orc.Config(**kw)))
+
+
+def test_plan_argument_errors(ffa):
+    bad = [dict(tsamp=0.0, period_min=1.0, period_max=2.0),
+           dict(tsamp=1e-3, period_min=2.0, period_max=1.0),
+           dict(tsamp=1e-3, period_min=1.0, period_max=2.0, downsample0=0),
+           dict(tsamp=1e-3, period_min=1.0, period_max=2.0, duty=0.0)]
+    for kw in bad:
+        with pytest.raises(ffa.FFAError) as ei:
+            ffa.Plan(ffa.Config(**kw), 1000)
+        assert ei.value.status == ffa.ERR_ARG
+    with pytest.raises(ffa.FFAError) as ei:
+        ffa.Plan(ffa.Config(tsamp=1e-3, period_min=1.0, period_max=2.0, widths=(1, 3)), 1000)
+    assert ei.value.status == ffa.ERR_UNSUPPORTED
+    # base periods beyond the scorer's 32768-bin envelope ask for pre-downsampling
+    with pytest.raises(ffa.FFAError) as ei:
+        ffa.Plan(ffa.Config(tsamp=1e-5, period_min=1.0, period_max=2.0), 1 << 22)
+    assert ei.value.status == ffa.ERR_UNSUPPORTED
+
+
+def test_empty_plan(ffa):
+    plan = ffa.Plan(ffa.Config(tsamp=1e-3, period_min=1.0, period_max=2.0), 10)
+    assert plan.n_trials == 0 and plan.n_periods == 0
+
+
+def test_workspace_covers_buffers(ffa):
+    plan = ffa.Plan(ffa.Config(**CONFIGS[1][1]), CONFIGS[1][0])
+    n0 = 1 << 26
+    biggest = int((plan.entries["m_rows"].astype(np.int64) * plan.entries["p0"]).max())
+    assert plan.workspace_bytes >= 8 * n0 * 2 + 4 * n0 + 8 * biggest
