@@ -168,6 +168,12 @@ def cpu_oracle_sample(kw, n, make, budget_s: float):
     import oracle
     oracle.build()
     threads = os.cpu_count() or 1
+    try:  # each base period folds in up to ~3 GB of host memory: bound the threads by it
+        with open("/proc/meminfo") as f:
+            avail_kb = next(int(l.split()[1]) for l in f if l.startswith("MemAvailable"))
+        threads = max(1, min(threads, int(avail_kb / (4 << 20))))
+    except (OSError, StopIteration, ValueError):
+        pass
     ocfg = oracle.Config(**{k: v for k, v in kw.items() if k != "widths"},
                          widths=kw.get("widths", ()), fold_type=oracle.FOLD_F64)
     rows, nt, win = oracle.plan(ocfg, n)

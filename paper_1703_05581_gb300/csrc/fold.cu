@@ -26,7 +26,6 @@
 
 namespace ffa {
 
-constexpr int FOLD_THREADS = 256;
 
 template <class T>
 struct FoldIn;
@@ -35,75 +34,98 @@ struct FoldIn<float> { using type = float; };
 template <>
 struct FoldIn<int32_t> { using type = int8_t; };
 
-// One pass of q stages.  first: read the series (rows >= m_data are zero)
-// instead of the previous plane.
+// Stage `wt` cyclic columns of a row starting at column `base` (< p0) into
+// shared memory: at most one wrap when wt <= p0, so the segment is two
+// contiguous runs; loads are unrolled so that several are in flight per lane.
+template <class T, class S>
+__device__ __forceinline__ void stage_row(T* __restrict__ rowp, const S* __restrict__ src, int64_t base,
+                                          int64_t p0, int wt, bool live, int lane) {
+    if (!live) {
+        for (int x = lane; x < wt; x += 32) rowp[x] = (T)0;
+        return;
+    }
+    if (wt <= p0) {
+        const int n1 = (int)((p0 - base) < wt ? (p0 - base) : wt);  // columns before the wrap
+        const S* a = src + base;
+#pragma unroll 4
+        for (int x = lane; x < n1; x += 32) rowp[x] = (T)a[x];
+#pragma unroll 4
+        for (int x = n1 + lane; x < wt; x += 32) rowp[x] = (T)src[x - n1];
+    } else {
+        int64_t col = base + lane;
+        while (col >= p0) col -= p0;
+        for (int x = lane; x < wt; x += 32) {
+            rowp[x] = (T)src[col];
+            col += 32;
+            while (col >= p0) col -= p0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One pass of q <= 5 stages.  A CTA owns (block, kappa, column tile): it
+// stages 2^q rows of B + 2^q - 1 columns in shared memory (row u starting at
+// column c + kappa*u, cyclically), runs the q local stages with one warp per
+// row (ping-pong buffers, conflict-free contiguous accesses) and writes 2^q
+// rows of B columns.
+// ---------------------------------------------------------------------------
+constexpr int FP_THREADS = 256;
+constexpr int FP_B = 256;
+
 template <class T, bool FIRST>
-__global__ void __launch_bounds__(FOLD_THREADS) k_fold_pass(
-    const void* __restrict__ src_v, T* __restrict__ dst, int64_t p0, int64_t m_rows,
-    int64_t m_data, int s, int q, int bw, int64_t n_ct) {
+__global__ void __launch_bounds__(FP_THREADS) k_fold_pass(const void* __restrict__ src_v,
+                                                          T* __restrict__ dst, int64_t p0,
+                                                          int64_t m_data, int s, int q, int64_t n_ct) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int rows = 1 << q;
-    const int wt = bw + rows - 1;  // staged width incl. halo
+    const int wt = FP_B + rows - 1;
     T* buf0 = reinterpret_cast<T*>(smem_raw);
     T* buf1 = buf0 + rows * wt;
-
     const int64_t unit = blockIdx.x;
     const int64_t ct = unit % n_ct;
     const int64_t rest = unit / n_ct;
     const int64_t kappa = rest & ((1ll << s) - 1);
     const int64_t blk = rest >> s;
-    const int64_t c = ct * bw;
+    const int64_t c = ct * FP_B;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NW = FP_THREADS / 32;
 
-    // stage the 2^q input rows
-    for (int u = threadIdx.x / 32; u < rows; u += FOLD_THREADS / 32) {
+    const int64_t kmod = kappa % p0;
+    for (int u = warp; u < rows; u += NW) {
         const int64_t g = blk * rows + u;  // group index at level s
-        int64_t base = (c + (kappa % p0) * (u % p0)) % p0;
-        T* rowp = buf0 + u * wt;
-        if (FIRST) {
-            const typename FoldIn<T>::type* z = (const typename FoldIn<T>::type*)src_v;
-            bool live = g < m_data;
-            const typename FoldIn<T>::type* zr = z + g * p0;
-            for (int x = threadIdx.x & 31; x < wt; x += 32) {
-                int64_t col = (base + x) % p0;
-                rowp[x] = live ? (T)zr[col] : (T)0;
-            }
-        } else {
-            const T* pl = (const T*)src_v + ((g << s) + kappa) * p0;
-            for (int x = threadIdx.x & 31; x < wt; x += 32) {
-                int64_t col = (base + x) % p0;
-                rowp[x] = pl[col];
-            }
-        }
+        int64_t base = c + (kmod * (u % p0)) % p0;
+        if (base >= p0) base -= p0;
+        if (FIRST)
+            stage_row(buf0 + u * wt, (const typename FoldIn<T>::type*)src_v + g * p0, base, p0, wt,
+                      g < m_data, lane);
+        else
+            stage_row(buf0 + u * wt, (const T*)src_v + ((g << s) + kappa) * p0, base, p0, wt, true, lane);
     }
     __syncthreads();
-
-    // q local stages
     T* in = buf0;
     T* out = buf1;
     for (int t = 1; t <= q; ++t) {
         const int half = 1 << (t - 1);
         const int width = wt - ((1 << t) - 1);
-        for (int r = threadIdx.x / 32; r < rows; r += FOLD_THREADS / 32) {
+        for (int r = warp; r < rows; r += NW) {
             const int gb = r & ~((1 << t) - 1);
             const int v = r - gb;
             const T* h = in + (gb + (v >> 1)) * wt;
             const T* tl = in + (gb + half + (v >> 1)) * wt + ((v + 1) >> 1);
             T* o = out + r * wt;
-            for (int x = threadIdx.x & 31; x < width; x += 32) o[x] = h[x] + tl[x];
+            for (int x = lane; x < width; x += 32) o[x] = h[x] + tl[x];
         }
         __syncthreads();
         T* tmp = in;
         in = out;
         out = tmp;
     }
-
-    // write 2^q output rows of the tile
     const int64_t out_row0 = (blk << (s + q)) + (kappa << q);
-    const int64_t ncols = (c + bw <= p0) ? bw : p0 - c;
-    for (int v = threadIdx.x / 32; v < rows; v += FOLD_THREADS / 32) {
+    const int64_t ncols = (c + FP_B <= p0) ? FP_B : p0 - c;
+    for (int v = warp; v < rows; v += NW) {
         T* d = dst + (out_row0 + v) * p0 + c;
         const T* sv = in + v * wt;
-        for (int x = threadIdx.x & 31; x < ncols; x += 32) d[x] = sv[x];
+        for (int x = lane; x < ncols; x += 32) d[x] = sv[x];
     }
 }
 
@@ -115,18 +137,203 @@ static int split_passes(int m, int qmax, int* qs) {
     return np;
 }
 
+// ---------------------------------------------------------------------------
+// Register-blocked pass (q = Q1 + Q2 <= 5 stages).  After staging the tile
+// as above, each thread takes 4 consecutive columns of one group of 2^Q1 rows,
+// loads them with aligned 128-bit shared-memory reads, applies Q1 stages in
+// registers (compile-time shifts) and stores its 2^Q1 partial trials already
+// shifted left by kappa1*u2, the column offset at which the second sub-pass
+// reads them; the second sub-pass then reads 128-bit aligned as well, applies
+// the remaining Q2 stages and writes the tile's output rows to global memory.
+// Neighbouring threads take neighbouring columns: conflict-free 16-byte reads.
+// ---------------------------------------------------------------------------
+template <class T, int QQ>
+struct RegStages {
+    static constexpr int R = 1 << QQ;
+    static constexpr int W = 4 + R - 1;      // columns needed for 4 outputs
+    static constexpr int NV = (W + 3) / 4;   // 128-bit loads per row
+    // rows: R pointers (16-byte aligned) into shared memory; out[v][0..3]
+    static __device__ __forceinline__ void run(const T* const* rowp, T (&out)[R][4]) {
+        T a[R][NV * 4];
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                *reinterpret_cast<int4*>(&a[u][4 * k]) = *reinterpret_cast<const int4*>(rowp[u] + 4 * k);
+#pragma unroll
+        for (int t = 1; t <= QQ; ++t) {
+            const int g = 1 << t, half = g >> 1;
+            T b[R][NV * 4];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int gb = r & ~(g - 1), v = r - gb;
+                const int hr = gb + (v >> 1), tr = gb + half + (v >> 1), sf = (v + 1) >> 1;
+#pragma unroll
+                for (int x = 0; x < W; ++x)
+                    if (x + g - 1 < W) b[r][x] = a[hr][x] + a[tr][x + sf];
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int x = 0; x < W; ++x) a[r][x] = b[r][x];
+        }
+#pragma unroll
+        for (int v = 0; v < R; ++v)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) out[v][x] = a[v][x];
+    }
+};
+
+constexpr int F4_THREADS = 256;
+constexpr int F4_B = 256;
+__host__ __device__ constexpr int f4_wa(int q) { return ((F4_B + (1 << q) - 1 + 3) & ~3) + 8; }
+__host__ __device__ constexpr int f4_wb(int q, int q1) { return ((F4_B + (1 << q) - (1 << q1) + 3) & ~3) + 8; }
+
+template <class T, bool FIRST, int Q1, int Q2>
+__global__ void __launch_bounds__(F4_THREADS, 2) k_fold_reg(const void* __restrict__ src_v,
+                                                           T* __restrict__ dst, int64_t p0,
+                                                           int64_t m_data, int s, int64_t n_ct) {
+    constexpr int q = Q1 + Q2;
+    constexpr int rows = 1 << q;
+    constexpr int R1 = 1 << Q1, R2 = 1 << Q2;
+    constexpr int WA = f4_wa(q), WB = f4_wb(q, Q1);
+    constexpr int W1 = F4_B + rows - R1;  // valid columns after the first sub-pass
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* bufA = reinterpret_cast<T*>(smem_raw);
+    T* bufB = bufA + rows * WA;
+
+    const int64_t unit = blockIdx.x;
+    const int64_t ct = unit % n_ct;
+    const int64_t rest = unit / n_ct;
+    const int64_t kappa = rest & ((1ll << s) - 1);
+    const int64_t blk = rest >> s;
+    const int64_t c = ct * F4_B;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NW = F4_THREADS / 32;
+    constexpr int WT = F4_B + rows - 1;  // staged columns
+
+    const int64_t kmod = kappa % p0;
+    for (int u = warp; u < rows; u += NW) {
+        const int64_t g = blk * rows + u;
+        int64_t base = c + (kmod * (u % p0)) % p0;
+        if (base >= p0) base -= p0;
+        if (FIRST)
+            stage_row(bufA + u * WA, (const typename FoldIn<T>::type*)src_v + g * p0, base, p0, WT,
+                      g < m_data, lane);
+        else
+            stage_row(bufA + u * WA, (const T*)src_v + ((g << s) + kappa) * p0, base, p0, WT, true, lane);
+    }
+    __syncthreads();
+    const int64_t grow0 = (blk << (s + q)) + (kappa << q);
+    const int64_t ncols = (c + F4_B <= p0) ? F4_B : p0 - c;
+
+    // first sub-pass: groups of R1 consecutive rows
+    {
+        constexpr int nstrips = (W1 + 3) / 4;
+        constexpr int items = (rows / R1) * nstrips;
+        for (int it = threadIdx.x; it < items; it += F4_THREADS) {
+            const int strip = it % nstrips, g = it / nstrips;
+            const int x0 = 4 * strip;
+            const T* rp[R1];
+#pragma unroll
+            for (int u = 0; u < R1; ++u) rp[u] = bufA + (g * R1 + u) * WA + x0;
+            T out[R1][4];
+            RegStages<T, Q1>::run(rp, out);
+            if (Q2 == 0) {
+#pragma unroll
+                for (int v = 0; v < R1; ++v) {
+                    T* d = dst + (grow0 + v) * p0 + c + x0;
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+                        if (x0 + x < ncols) d[x] = out[v][x];
+                }
+            } else {
+                // group g is input row u2 = g of the second sub-pass; trial v of it is
+                // read at column offset v*u2: store it shifted left by that much
+                const int u2 = g;
+#pragma unroll
+                for (int v = 0; v < R1; ++v) {
+                    T* d = bufB + (v * R2 + u2) * WB;
+                    const int sh = v * u2;
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) {
+                        const int xx = x0 + x - sh;
+                        if (xx >= 0 && x0 + x < W1) d[xx] = out[v][x];
+                    }
+                }
+            }
+        }
+    }
+    if (Q2 > 0) {
+        __syncthreads();
+        constexpr int nstrips = F4_B / 4;
+        constexpr int items = R1 * nstrips;
+        for (int it = threadIdx.x; it < items; it += F4_THREADS) {
+            const int strip = it % nstrips, k1 = it / nstrips;
+            const int x0 = 4 * strip;
+            const T* rp[R2];
+#pragma unroll
+            for (int u = 0; u < R2; ++u) rp[u] = bufB + (k1 * R2 + u) * WB + x0;
+            T out[R2][4];
+            RegStages<T, Q2>::run(rp, out);
+#pragma unroll
+            for (int v = 0; v < R2; ++v) {
+                T* d = dst + (grow0 + k1 * R2 + v) * p0 + c + x0;
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+                    if (x0 + x < ncols) d[x] = out[v][x];
+            }
+        }
+    }
+}
+
+template <class T, bool FIRST, int Q1, int Q2>
+static ffa_status launch_reg(const void* src, T* dst, int64_t p0, int64_t m_rows, int64_t m_data,
+                             int s, cudaStream_t st) {
+    constexpr int q = Q1 + Q2;
+    constexpr int rows = 1 << q;
+    const size_t smem = sizeof(T) * ((size_t)rows * f4_wa(q) + (Q2 > 0 ? (size_t)rows * f4_wb(q, Q1) : 0));
+    ffa_status es = ensure_smem((const void*)k_fold_reg<T, FIRST, Q1, Q2>, smem);
+    if (es != FFA_OK) return es;
+    const int64_t n_ct = (p0 + F4_B - 1) / F4_B;
+    const int64_t units = (m_rows / rows) * n_ct;
+    k_fold_reg<T, FIRST, Q1, Q2><<<(unsigned)units, F4_THREADS, smem, st>>>(src, dst, p0, m_data, s, n_ct);
+    FFA_LAUNCH_CHECK("k_fold_reg");
+    count_launch();
+    return FFA_OK;
+}
+
+template <class T, bool FIRST>
+static ffa_status pass_q(int q, const void* src, T* dst, int64_t p0, int64_t m_rows, int64_t m_data,
+                         int s, cudaStream_t st) {
+    switch (q) {
+        case 1: return launch_reg<T, FIRST, 1, 0>(src, dst, p0, m_rows, m_data, s, st);
+        case 2: return launch_reg<T, FIRST, 2, 0>(src, dst, p0, m_rows, m_data, s, st);
+        case 3: return launch_reg<T, FIRST, 3, 0>(src, dst, p0, m_rows, m_data, s, st);
+        case 4: return launch_reg<T, FIRST, 2, 2>(src, dst, p0, m_rows, m_data, s, st);
+        case 5: return launch_reg<T, FIRST, 3, 2>(src, dst, p0, m_rows, m_data, s, st);
+        default: break;
+    }
+    const int rows = 1 << q;
+    const size_t smem = 2 * sizeof(T) * (size_t)rows * (FP_B + rows - 1);
+    ffa_status es = ensure_smem((const void*)k_fold_pass<T, FIRST>, smem);
+    if (es != FFA_OK) return es;
+    const int64_t n_ct = (p0 + FP_B - 1) / FP_B;
+    const int64_t units = (m_rows / rows) * n_ct;
+    k_fold_pass<T, FIRST><<<(unsigned)units, FP_THREADS, smem, st>>>(src, dst, p0, m_data, s, q, n_ct);
+    FFA_LAUNCH_CHECK("k_fold_pass");
+    count_launch();
+    return FFA_OK;
+}
+
 template <class T>
 static ffa_status fold_impl(const void* d_z, int64_t p0, int64_t m_data, int64_t m_rows,
-                            T* d_plane, T* d_tmp, cudaStream_t st) {
-    int m = 0;
-    while ((1ll << m) < m_rows) ++m;
+                            int stages, T* d_plane, T* d_tmp, cudaStream_t st) {
     const int qmax = 5;
-    const int bw = p0 < 256 ? (int)p0 : 256;
-    const int64_t n_ct = (p0 + bw - 1) / bw;
     int qs[64];
-    int np = split_passes(m, qmax, qs);
+    int np = split_passes(stages, qmax, qs);
     if (np == 0) {
-        // a single row: the fold is the row itself
+        // no stage to run: copy the (zero-padded) rows
         np = 1;
         qs[0] = 0;
     }
@@ -134,35 +341,27 @@ static ffa_status fold_impl(const void* d_z, int64_t p0, int64_t m_data, int64_t
     T* bufs[2] = {d_plane, d_tmp};
     int s = 0;
     for (int pi = 0; pi < np; ++pi) {
-        int q = qs[pi];
         T* dst = bufs[(np - 1 - pi) & 1];
         const void* src = pi == 0 ? d_z : (const void*)bufs[(np - pi) & 1];
-        int rows = 1 << q;
-        size_t smem = 2 * (size_t)rows * (bw + rows - 1) * sizeof(T);
-        int64_t units = (m_rows >> q) * n_ct;
-        if (pi == 0) {
-            ffa_status es = ensure_smem((const void*)k_fold_pass<T, true>, smem);
-            if (es != FFA_OK) return es;
-            k_fold_pass<T, true><<<(unsigned)units, FOLD_THREADS, smem, st>>>(
-                src, dst, p0, m_rows, m_data, s, q, bw, n_ct);
-        } else {
-            ffa_status es = ensure_smem((const void*)k_fold_pass<T, false>, smem);
-            if (es != FFA_OK) return es;
-            k_fold_pass<T, false><<<(unsigned)units, FOLD_THREADS, smem, st>>>(
-                src, dst, p0, m_rows, m_data, s, q, bw, n_ct);
-        }
-        FFA_LAUNCH_CHECK("k_fold_pass");
-        count_launch();
-        s += q;
+        ffa_status e = pi == 0 ? pass_q<T, true>(qs[pi], src, dst, p0, m_rows, m_data, s, st)
+                               : pass_q<T, false>(qs[pi], src, dst, p0, m_rows, m_data, s, st);
+        if (e != FFA_OK) return e;
+        s += qs[pi];
     }
     return FFA_OK;
 }
 
+// Run the first `stages` FFA stages (all of them when stages < 0).  With
+// fewer stages the plane holds, per group of 2^stages rows, its partial
+// trials (row g * 2^stages + kappa); zero stages copy the (zero-padded) rows.
 ffa_status launch_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
-                       int64_t m_rows, void* d_plane, void* d_tmp, cudaStream_t st) {
+                       int64_t m_rows, int stages, void* d_plane, void* d_tmp, cudaStream_t st) {
+    int m = 0;
+    while ((1ll << m) < m_rows) ++m;
+    if (stages < 0 || stages > m) stages = m;
     if (precision == FFA_FOLD_F32)
-        return fold_impl<float>(d_z, p0, m_data, m_rows, (float*)d_plane, (float*)d_tmp, st);
-    return fold_impl<int32_t>(d_z, p0, m_data, m_rows, (int32_t*)d_plane, (int32_t*)d_tmp, st);
+        return fold_impl<float>(d_z, p0, m_data, m_rows, stages, (float*)d_plane, (float*)d_tmp, st);
+    return fold_impl<int32_t>(d_z, p0, m_data, m_rows, stages, (int32_t*)d_plane, (int32_t*)d_tmp, st);
 }
 
 }  // namespace ffa

@@ -26,11 +26,13 @@ ffa_status launch_detrend(const double* d_raw, int64_t n, int32_t window, double
 ffa_status launch_normalise(const double* d_resid, int64_t n, int32_t precision, void* d_out,
                             double* d_stats, cudaStream_t st);
 ffa_status launch_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
-                       int64_t m_rows, void* d_plane, void* d_tmp, cudaStream_t st);
-ffa_status launch_score(const void* d_prof, int32_t precision, int64_t count, int64_t p0,
-                        const ScoreWidths& wd, ffa_record* d_rec, int32_t* d_status,
-                        cudaStream_t st);
-size_t score_smem_bytes(int64_t p0);
+                       int64_t m_rows, int stages, void* d_plane, void* d_tmp, cudaStream_t st);
+// Algorithm 1 on `count` trials starting at trial0.  fused: d_prof is the
+// plane after all but the last FFA stage (m_rows rows); the kernel applies the
+// last stage while loading.  Otherwise d_prof holds ready profiles.
+ffa_status launch_score2(const void* d_prof, int32_t precision, bool fused, int64_t count,
+                         int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
+                         ffa_record* d_rec, int32_t* d_status, cudaStream_t st);
 
 constexpr int STATS_DOUBLES = 2 + 1024;  // {mean, std} + reduction partials
 

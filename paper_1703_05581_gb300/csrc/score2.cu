@@ -1,0 +1,882 @@
+// Algorithm 1 (Section 2.2.1, Eq. 3-4) on the GPU, one 1024-thread CTA per
+// folded profile, with the last FFA stage (Section 2.1) fused into the load.
+//
+// Layout.  The profile x (p0 bins) is extended cyclically to p0 + wmax bins
+// and cut into blocks of 32 consecutive bins; thread t owns block t in
+// registers.  Blocks beyond the first 1024 (long profiles) only take part in
+// the prefix step.
+//
+// Median and MAD (exact).  A monotone bucket function (affine map of the
+// value, rounded, clamped) feeds a 2048-bin shared-memory histogram; the
+// bucket(s) holding the wanted ranks are gathered and sorted, which gives the
+// exact order statistics because a monotone bucket map preserves order
+// between buckets.  For float profiles the deviations |x - med| are bucketed
+// from their FP32 values |x - fl(med)|, which differ from the exact FP64
+// deviations by at most E = max|x| * 2^-20; gathering one extra bucket on each
+// side (more when E is large against a bucket) catches every sample whose
+// exact deviation can be the MAD, and those few are re-evaluated in FP64.
+// If a gather overflows its buffer, an exact radix select over the register
+// values takes over.
+//
+// Box sums.  With the in-block exclusive prefix c_t[o] (FP32) and the block
+// offsets Cb[t] = sum of earlier blocks (float-float), the cyclic box sum of
+// width w >= 32 starting at bin 32t + o is
+//     (Cb[t + w/32] - Cb[t]) + (c_{t+w/32}[o] - c_t[o]),
+// one shared-memory read, two adds and a max per bin; widths below 32 use the
+// thread's own prefix and the next block's.  Int profiles use the same
+// formulas in wrapping int32 arithmetic, which is exact for box sums below
+// 2^31.  Only the maximum of each width is kept; the winning width's first
+// argmax is found afterwards by recomputing that width, bit-identically.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ffa {
+
+namespace {
+
+constexpr int T2 = 1024;          // threads per CTA
+constexpr int R2 = 32;            // bins per block (per thread)
+constexpr int MAXB = 2048;        // max blocks incl. the cyclic extension (65536 bins)
+constexpr int NBK = 2048;         // histogram buckets
+constexpr int CAPM = 1024;        // gather capacity
+constexpr double KMAD = 1.4826;   // printed after Eq. 4
+
+// Shared-memory index of bin t: 4 pad words per 32-bin block keep every block
+// 16-byte aligned (vector loads) and spread blocked accesses over the banks.
+__device__ __forceinline__ int sidx(int t) { return t + 4 * (t >> 5); }
+
+struct Sh2 {
+    uint32_t hist[NBK];
+    double cand[CAPM];
+    float cbh[MAXB + 1];  // block offsets (hi) / int offsets reinterpreted
+    float cbl[MAXB + 1];  // block offsets (lo)
+    float wred[16][32];   // per-width warp maxima (float profiles)
+    int wredi[16][32];    // per-width warp maxima (int profiles)
+    float fred[32];
+    double dred[64];
+    int ired[32];
+    uint32_t cnt, below;
+    int bin_a, bin_b;
+    uint32_t below_a, below_b;
+    int phase;
+};
+
+// ---- block helpers (T2 threads) --------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_maxi(int v) {
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ int warp_mini(int v) {
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ float blk_sum(float v, Sh2& sh) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sh.fred[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = warp_sum(sh.fred[threadIdx.x & 31]);
+    __syncthreads();
+    return r;
+}
+// block sums of a and b and the max of c (one barrier pair)
+__device__ void blk_stats(float& a, float& b, float& c, Sh2& sh) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_max(c);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sh.fred[w] = a;
+        sh.wred[0][w] = b;
+        sh.wred[1][w] = c;
+    }
+    __syncthreads();
+    a = warp_sum(sh.fred[l]);
+    b = warp_sum(sh.wred[0][l]);
+    c = warp_max(sh.wred[1][l]);
+    __syncthreads();
+}
+__device__ float blk_max(float v, Sh2& sh) {
+    v = warp_max(v);
+    if ((threadIdx.x & 31) == 0) sh.fred[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = warp_max(sh.fred[threadIdx.x & 31]);
+    __syncthreads();
+    return r;
+}
+__device__ int blk_mini(int v, Sh2& sh) {
+    v = warp_mini(v);
+    if ((threadIdx.x & 31) == 0) sh.ired[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int r = warp_mini(sh.ired[threadIdx.x & 31]);
+    __syncthreads();
+    return r;
+}
+
+// exclusive scan of one uint32 per thread
+__device__ uint32_t blk_exscan_u(uint32_t v, Sh2& sh, uint32_t* total) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+    }
+    uint32_t* s = reinterpret_cast<uint32_t*>(sh.ired);
+    if (lane == 31) s[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t y = s[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t u = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += u;
+        }
+        s[lane] = y;
+    }
+    __syncthreads();
+    uint32_t r = (warp ? s[warp - 1] : 0u) + x - v;
+    if (total) *total = s[31];
+    __syncthreads();
+    return r;
+}
+
+// exclusive scan of float-float values (hi, lo) in block order
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float& sh_, float& sl_) {
+    float s, e;
+    two_sum(ah, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(al, bl));
+    float s2 = __fadd_rn(s, e);
+    sl_ = __fsub_rn(e, __fsub_rn(s2, s));
+    sh_ = s2;
+}
+
+__device__ void blk_exscan_ff(float vh, Sh2& sh, float& oh, float& ol, float& th, float& tl) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float xh = vh, xl = 0.0f;
+    for (int o = 1; o < 32; o <<= 1) {
+        float uh = __shfl_up_sync(0xffffffffu, xh, o);
+        float ul = __shfl_up_sync(0xffffffffu, xl, o);
+        if (lane >= o) ff_add(xh, xl, uh, ul, xh, xl);
+    }
+    // inclusive warp result in (xh, xl)
+    if (lane == 31) {
+        sh.fred[warp] = xh;
+        sh.wred[0][warp] = xl;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float yh = sh.fred[lane], yl = sh.wred[0][lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            float uh = __shfl_up_sync(0xffffffffu, yh, o);
+            float ul = __shfl_up_sync(0xffffffffu, yl, o);
+            if (lane >= o) ff_add(yh, yl, uh, ul, yh, yl);
+        }
+        sh.fred[lane] = yh;
+        sh.wred[0][lane] = yl;
+    }
+    __syncthreads();
+    float bh = warp ? sh.fred[warp - 1] : 0.0f, bl = warp ? sh.wred[0][warp - 1] : 0.0f;
+    // exclusive = base + inclusive - own  ->  compute base + (inclusive warp prefix excluding own)
+    float eh, el;
+    {
+        float ph = __shfl_up_sync(0xffffffffu, xh, 1), pl = __shfl_up_sync(0xffffffffu, xl, 1);
+        if (lane == 0) {
+            ph = 0.0f;
+            pl = 0.0f;
+        }
+        ff_add(bh, bl, ph, pl, eh, el);
+    }
+    oh = eh;
+    ol = el;
+    th = sh.fred[31];
+    tl = sh.wred[0][31];
+    __syncthreads();
+}
+
+// ranks ra <= rb -> their bins and the counts below those bins, one scan
+__device__ void blk_find2(Sh2& sh, uint32_t ra, uint32_t rb) {
+    const int per = NBK / T2;
+    const int b0 = threadIdx.x * per;
+    uint32_t s = 0;
+    for (int t = 0; t < per; ++t) s += sh.hist[b0 + t];
+    const uint32_t ex = blk_exscan_u(s, sh, nullptr);
+    uint32_t c = ex;
+    for (int t = 0; t < per; ++t) {
+        const uint32_t h = sh.hist[b0 + t];
+        if (ra >= c && ra < c + h) {
+            sh.bin_a = b0 + t;
+            sh.below_a = c;
+        }
+        if (rb >= c && rb < c + h) {
+            sh.bin_b = b0 + t;
+            sh.below_b = c;
+        }
+        c += h;
+    }
+    __syncthreads();
+}
+
+// single-rank variant (radix fallback)
+__device__ void blk_find(Sh2& sh, uint32_t rank, int* bin, uint32_t* below) {
+    blk_find2(sh, rank, rank);
+    *bin = sh.bin_a;
+    *below = sh.below_a;
+    __syncthreads();
+}
+
+// Values of ranks ta <= tb among sh.cand[0..n) (ties broken by index): the
+// n x n comparisons are spread over the whole CTA, each candidate's rank is
+// accumulated in shared memory (sh.hist is free at this point).
+__device__ void cand_pick2(Sh2& sh, uint32_t n, uint32_t ta, uint32_t tb, double* va, double* vb) {
+    for (uint32_t i = threadIdx.x; i < n; i += T2) sh.hist[i] = 0;
+    __syncthreads();
+    const uint32_t chunks = (T2 + n - 1) / (n ? n : 1);  // threads per candidate
+    const uint32_t pairs = n * chunks;
+    for (uint32_t p = threadIdx.x; p < pairs; p += T2) {
+        const uint32_t i = p % n, part = p / n;
+        const double ci = sh.cand[i];
+        uint32_t rk = 0;
+        for (uint32_t j = part; j < n; j += chunks) {
+            const double cj = sh.cand[j];
+            rk += (cj < ci) || (cj == ci && j < i);
+        }
+        if (rk) atomicAdd(&sh.hist[i], rk);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += T2) {
+        const uint32_t rk = sh.hist[i];
+        if (rk == ta) sh.dred[1] = sh.cand[i];
+        if (rk == tb) sh.dred[2] = sh.cand[i];
+    }
+    __syncthreads();
+    *va = sh.dred[1];
+    *vb = sh.dred[2];
+    __syncthreads();
+}
+
+// Exact rank-`rank` 64-bit key of keyf(j), j < n, by an 8-pass radix select
+// over the profile still held in shared memory (fallback when a gather
+// overflows; rare).
+template <class KeyF>
+__device__ __noinline__ uint64_t smem_select64(Sh2& sh, int n, uint32_t rank, KeyF keyf) {
+    uint64_t prefix = 0, mask = 0;
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 56 - 8 * pass;
+        for (int b = threadIdx.x; b < NBK; b += T2) sh.hist[b] = 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += T2) {
+            const uint64_t kk = keyf(j);
+            if ((kk & mask) == prefix) atomicAdd(&sh.hist[(kk >> shift) & 0xff], 1u);
+        }
+        __syncthreads();
+        blk_find(sh, rank, &sh.bin_a, &sh.below_a);
+        rank -= sh.below_a;
+        prefix |= (uint64_t)sh.bin_a << shift;
+        mask |= (uint64_t)0xff << shift;
+        __syncthreads();
+    }
+    return prefix;
+}
+
+template <class T>
+struct Traits;
+template <>
+struct Traits<float> {
+    static constexpr bool is_int = false;
+};
+template <>
+struct Traits<int32_t> {
+    static constexpr bool is_int = true;
+};
+
+// bucket of a float value: rint((v - base) * inv + NBK/2) clamped, monotone in v
+__device__ __forceinline__ int fbucket(float v, float base, float inv) {
+    float f = __fmaf_rn(__fsub_rn(v, base), inv, (float)(NBK / 2));
+    f = fminf(fmaxf(f, 0.0f), (float)(NBK - 1));
+    return __float_as_int(__fadd_rn(f, 12582912.0f)) - 0x4B400000;
+}
+// int profiles (|x| < 2^28): floor((v - base) / 2^sh) + NBK/2, clamped; monotone
+__device__ __forceinline__ int ibucket(int v, int base, int sh) {
+    const int d = ((v - base) >> sh) + NBK / 2;  // arithmetic shift = floor division
+    return d < 0 ? 0 : (d > NBK - 1 ? NBK - 1 : d);
+}
+
+}  // namespace
+
+// Box-sum helpers.  C(32t + o) = Cb[t] + c_t[o]; a box of width w at bin
+// 32t + r is C(32t + r + w) - C(32t + r).
+template <class T>
+struct BoxOps;
+template <>
+struct BoxOps<float> {
+    static __device__ __forceinline__ float blockdiff(const Sh2& sh, int b2, int b1) {
+        return __fadd_rn(__fsub_rn(sh.cbh[b2], sh.cbh[b1]), __fsub_rn(sh.cbl[b2], sh.cbl[b1]));
+    }
+    static __device__ __forceinline__ float box(float D, float c2, float c1) {
+        return __fadd_rn(D, __fsub_rn(c2, c1));
+    }
+    static __device__ __forceinline__ float diff(float c2, float c1) { return __fsub_rn(c2, c1); }
+    static __device__ __forceinline__ float lowest() { return -INFINITY; }
+};
+template <>
+struct BoxOps<int32_t> {
+    static __device__ __forceinline__ int32_t blockdiff(const Sh2& sh, int b2, int b1) {
+        const int* cbi = reinterpret_cast<const int*>(sh.cbh);
+        return (int32_t)((uint32_t)cbi[b2] - (uint32_t)cbi[b1]);
+    }
+    static __device__ __forceinline__ int32_t box(int32_t D, int32_t c2, int32_t c1) {
+        return (int32_t)((uint32_t)D + ((uint32_t)c2 - (uint32_t)c1));
+    }
+    static __device__ __forceinline__ int32_t diff(int32_t c2, int32_t c1) {
+        return (int32_t)((uint32_t)c2 - (uint32_t)c1);
+    }
+    static __device__ __forceinline__ int32_t lowest() { return INT32_MIN; }
+};
+
+// Width W < 32 (compile time): own prefix, next block past the end.  With
+// FIND, returns the first position whose box equals `target` (else -1).
+template <class T, int W, bool FIND>
+__device__ __forceinline__ T small_width(const T (&c)[R2], const Sh2& sh, const T* buf, int tid,
+                                         int nvalid, T target, int* first) {
+    using B = BoxOps<T>;
+    const T Town = B::blockdiff(sh, tid + 1, tid);
+    constexpr int NC = W < 4 ? 4 : W;  // next block's first values, 128-bit loads
+    T cn[NC];
+    const T* nb = buf + sidx((tid + 1) * R2);
+#pragma unroll
+    for (int k = 0; k < NC; k += 4) *reinterpret_cast<int4*>(&cn[k]) = *reinterpret_cast<const int4*>(nb + k);
+    T m0 = B::lowest(), m1 = B::lowest();
+#pragma unroll
+    for (int r = 0; r < R2; ++r) {
+        T bx;
+        if (r + W < R2) bx = B::diff(c[r + W], c[r]);
+        else bx = B::box(Town, cn[r + W - R2], c[r]);
+        if (r < nvalid) {
+            if (r & 1) m1 = bx > m1 ? bx : m1;
+            else m0 = bx > m0 ? bx : m0;
+            if (FIND && *first < 0 && bx == target) *first = r;
+        }
+    }
+    return m0 > m1 ? m0 : m1;
+}
+
+// Width w >= 32 (multiple of 32): block tid + w/32 at the same offsets.
+template <class T, bool FIND>
+__device__ __forceinline__ T wide_width(const T (&c)[R2], const Sh2& sh, const T* buf, int tid,
+                                        int w, int nvalid, T target, int* first) {
+    using B = BoxOps<T>;
+    const int b2 = tid + w / R2;
+    const T D = B::blockdiff(sh, b2, tid);
+    const int o2 = b2 * R2;
+    T m = B::lowest();
+#pragma unroll
+    for (int r = 0; r < R2; ++r) {
+        T bx = B::box(D, buf[sidx(o2 + r)], c[r]);
+        if (r < nvalid) {
+            m = bx > m ? bx : m;
+            if (FIND && *first < 0 && bx == target) *first = r;
+        }
+    }
+    return m;
+}
+
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+
+// Wide widths, float profiles, maxima only: the same per-bin arithmetic as
+// wide_width (D + (c2 - c1), each rounded to nearest) on packed pairs.
+__device__ __forceinline__ float wide_width_f32x2(const float (&c)[R2], const Sh2& sh, const float* buf,
+                                                  int tid, int w, int nvalid) {
+    const int b2 = tid + w / R2;
+    const float D = BoxOps<float>::blockdiff(sh, b2, tid);
+    const unsigned long long DD = pk2(D, D);
+    const float* cb = buf + sidx(b2 * R2);
+    float m = -INFINITY, ma = -INFINITY;
+#pragma unroll
+    for (int r = 0; r < R2; r += 4) {
+        const float4 c2 = *reinterpret_cast<const float4*>(cb + r);
+        unsigned long long s01, s23, b01, b23;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(s01) : "l"(pk2(c2.x, c2.y)), "l"(pk2(c[r], c[r + 1])));
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(s23) : "l"(pk2(c2.z, c2.w)), "l"(pk2(c[r + 2], c[r + 3])));
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(b01) : "l"(DD), "l"(s01));
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(b23) : "l"(DD), "l"(s23));
+        float v0, v1, v2, v3;
+        upk2(b01, v0, v1);
+        upk2(b23, v2, v3);
+        if (r + 0 < nvalid) m = fmaxf(m, v0);
+        if (r + 1 < nvalid) ma = fmaxf(ma, v1);
+        if (r + 2 < nvalid) m = fmaxf(m, v2);
+        if (r + 3 < nvalid) ma = fmaxf(ma, v3);
+    }
+    return fmaxf(m, ma);
+}
+
+template <class T, bool FIND>
+__device__ __forceinline__ T width_max(const T (&c)[R2], const Sh2& sh, const T* buf, int tid, int w,
+                                       int nvalid, T target, int* first) {
+    switch (w) {
+        case 1: return small_width<T, 1, FIND>(c, sh, buf, tid, nvalid, target, first);
+        case 2: return small_width<T, 2, FIND>(c, sh, buf, tid, nvalid, target, first);
+        case 4: return small_width<T, 4, FIND>(c, sh, buf, tid, nvalid, target, first);
+        case 8: return small_width<T, 8, FIND>(c, sh, buf, tid, nvalid, target, first);
+        case 16: return small_width<T, 16, FIND>(c, sh, buf, tid, nvalid, target, first);
+        default:
+            if constexpr (!FIND && !Traits<T>::is_int) return wide_width_f32x2(c, sh, buf, tid, w, nvalid);
+            else return wide_width<T, FIND>(c, sh, buf, tid, w, nvalid, target, first);
+    }
+}
+
+// prof: FUSED ? the stage-(m-1) plane (m_rows rows of p0) : profiles of p0.
+// Record blockIdx.x belongs to trial trial0 + blockIdx.x.
+template <class T, bool FUSED>
+__global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, int64_t p0_,
+                                                  int64_t m_rows, int64_t trial0, ScoreWidths wd,
+                                                  ffa_record* __restrict__ rec, int32_t* d_status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Sh2& sh = *reinterpret_cast<Sh2*>(smem_raw);
+    T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(Sh2) + 15) & ~(size_t)15));
+    using B = BoxOps<T>;
+    const int p0 = (int)p0_;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int64_t k = trial0 + blockIdx.x;
+    const int wmax = wd.w[wd.n - 1];
+    const int nbe = (p0 + wmax + R2) / R2 + 1;  // blocks incl. the cyclic extension
+
+    // ---- load; fused last FFA stage: head row k>>1 plus tail row M/2 + (k>>1)
+    // read ceil(k/2) bins further on
+    const T* hrow;
+    const T* trow = nullptr;
+    int sft = 0;
+    if (FUSED && m_rows > 1) {
+        hrow = prof + (k >> 1) * p0_;
+        trow = prof + ((m_rows >> 1) + (k >> 1)) * p0_;
+        sft = (int)(((k + 1) >> 1) % p0_);
+    } else if (FUSED) {
+        hrow = prof;
+    } else {
+        hrow = prof + k * p0_;
+    }
+    if (trow) {
+        // the tail row read from column sft on: two contiguous runs
+        const int n1 = p0 - sft;
+#pragma unroll 4
+        for (int j = tid; j < p0; j += T2) {
+            const T t = j < n1 ? trow[j + sft] : trow[j - n1];
+            buf[sidx(j)] = hrow[j] + t;
+        }
+    } else {
+#pragma unroll 4
+        for (int j = tid; j < p0; j += T2) buf[sidx(j)] = hrow[j];
+    }
+    __syncthreads();
+    T x[R2];
+    const int base_pos = tid * R2;
+    int nvalid = p0 - base_pos;
+    nvalid = nvalid < 0 ? 0 : (nvalid > R2 ? R2 : nvalid);
+    {
+        const T* blk = buf + sidx(base_pos);
+#pragma unroll
+        for (int r = 0; r < R2; r += 4) {
+            T v4[4];
+            *reinterpret_cast<int4*>(v4) = *reinterpret_cast<const int4*>(blk + r);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[r + i] = (r + i < nvalid) ? v4[i] : (T)0;
+        }
+    }
+
+    // ---- median (Eq. 3), exact ----
+    const uint32_t r1 = (uint32_t)((p0 - 1) / 2), r2 = (uint32_t)(p0 / 2);
+    float fs = 0.0f, fq = 0.0f, famax = 0.0f;
+    if (nvalid > 0) {
+#pragma unroll
+        for (int r = 0; r < R2; ++r)
+            if (r < nvalid) {
+                float v = (float)x[r];
+                fs += v;
+                fq = fmaf(v, v, fq);
+                famax = fmaxf(famax, fabsf(v));
+            }
+    }
+    blk_stats(fs, fq, famax, sh);
+    const float mean = fs / (float)p0;
+    const float msq = fq / (float)p0;
+    const float amax = famax;
+    float sig = sqrtf(fmaxf(msq - mean * mean, 0.0f));
+    if (!(sig > 0.0f)) sig = fmaxf(amax, 1.0f);
+
+    for (int b = tid; b < NBK; b += T2) sh.hist[b] = 0;
+    if (tid == 0) {
+        sh.cnt = 0;
+        sh.below = 0;
+    }
+    __syncthreads();
+    const float inv_m = (float)NBK / (8.0f * sig);
+    int ish = 0;
+    int ibase = 0;
+    if constexpr (Traits<T>::is_int) {
+        ibase = (int)floorf(mean);
+        const double span = 8.0 * (double)sig / (double)NBK;
+        while ((double)(1ll << ish) < span && ish < 40) ++ish;
+    }
+    auto bucket_m = [&](T v) -> int {
+        if constexpr (Traits<T>::is_int) return ibucket((int)v, ibase, ish);
+        else return fbucket((float)v, mean, inv_m);
+    };
+    if (nvalid > 0) {
+#pragma unroll
+        for (int r = 0; r < R2; ++r)
+            if (r < nvalid) atomicAdd(&sh.hist[bucket_m(x[r])], 1u);
+    }
+    __syncthreads();
+    blk_find2(sh, r1, r2);
+    const int mb1 = sh.bin_a, mb2 = sh.bin_b;
+    const uint32_t mbelow = sh.below_a;
+    if (nvalid > 0) {
+#pragma unroll
+        for (int r = 0; r < R2; ++r)
+            if (r < nvalid) {
+                int b = bucket_m(x[r]);
+                if (b >= mb1 && b <= mb2) {
+                    uint32_t s = atomicAdd(&sh.cnt, 1u);
+                    if (s < CAPM) sh.cand[s] = (double)x[r];
+                }
+            }
+    }
+    __syncthreads();
+    double med;
+    {
+        const uint32_t cc = sh.cnt;
+        if (cc <= CAPM) {
+            double a, b;
+            cand_pick2(sh, cc, r1 - mbelow, r2 - mbelow, &a, &b);
+            med = (r1 == r2) ? a : (a + b) / 2;
+        } else {
+            const T* vb = buf;
+            auto key = [vb](int j) -> uint64_t {
+                if constexpr (Traits<T>::is_int) return (uint64_t)ikey((int32_t)vb[sidx(j)]);
+                else return (uint64_t)fkey((float)vb[sidx(j)]);
+            };
+            const uint64_t ka = smem_select64(sh, p0, r1, key);
+            const uint64_t kb = (r1 == r2) ? ka : smem_select64(sh, p0, r2, key);
+            double a, b;
+            if constexpr (Traits<T>::is_int) {
+                a = (double)(int32_t)((uint32_t)ka ^ 0x80000000u);
+                b = (double)(int32_t)((uint32_t)kb ^ 0x80000000u);
+            } else {
+                a = (double)fkey_inv((uint32_t)ka);
+                b = (double)fkey_inv((uint32_t)kb);
+            }
+            med = (r1 == r2) ? a : (a + b) / 2;
+        }
+        __syncthreads();
+    }
+
+    // ---- MAD (Eq. 3), exact ----
+    double mad;
+    for (int b = tid; b < NBK; b += T2) sh.hist[b] = 0;
+    if (tid == 0) {
+        sh.cnt = 0;
+        sh.below = 0;
+    }
+    __syncthreads();
+    if constexpr (Traits<T>::is_int) {
+        // e = |2x - (a + b)| is exact; the deviation is e / 2
+        const int s2 = (int)llrint(2.0 * med);
+        int esh = 0;
+        const double span = 8.0 * (double)sig / (double)NBK;
+        while ((double)(1ll << esh) < span && esh < 40) ++esh;
+        auto eval = [&](T v) -> int {
+            const int e = 2 * (int)v - s2;
+            return e < 0 ? -e : e;
+        };
+        auto eb = [&](int e) -> int {
+            const int b = e >> esh;
+            return b > NBK - 1 ? NBK - 1 : b;
+        };
+        if (nvalid > 0) {
+#pragma unroll
+            for (int r = 0; r < R2; ++r)
+                if (r < nvalid) atomicAdd(&sh.hist[eb(eval(x[r]))], 1u);
+        }
+        __syncthreads();
+        blk_find2(sh, r1, r2);
+        const int c1 = sh.bin_a, c2 = sh.bin_b;
+        const uint32_t cbel = sh.below_a;
+        if (nvalid > 0) {
+#pragma unroll
+            for (int r = 0; r < R2; ++r)
+                if (r < nvalid) {
+                    const int e = eval(x[r]);
+                    const int b = eb(e);
+                    if (b >= c1 && b <= c2) {
+                        uint32_t s = atomicAdd(&sh.cnt, 1u);
+                        if (s < CAPM) sh.cand[s] = (double)e;
+                    }
+                }
+        }
+        __syncthreads();
+        const uint32_t cc = sh.cnt;
+        if (cc <= CAPM) {
+            double e1, e2;
+            cand_pick2(sh, cc, r1 - cbel, r2 - cbel, &e1, &e2);
+            mad = (r1 == r2) ? e1 / 2 : (e1 + e2) / 4;
+        } else {
+            const T* vb = buf;
+            auto key = [vb, s2](int j) -> uint64_t {
+                const int e = 2 * (int)vb[sidx(j)] - s2;
+                return (uint64_t)(uint32_t)(e < 0 ? -e : e);
+            };
+            const uint64_t e1 = smem_select64(sh, p0, r1, key);
+            const uint64_t e2 = (r1 == r2) ? e1 : smem_select64(sh, p0, r2, key);
+            mad = (r1 == r2) ? (double)e1 / 2 : ((double)e1 + (double)e2) / 4;
+        }
+        __syncthreads();
+    } else {
+        const float m32 = __double2float_rn(med);
+        const float E = ldexpf(amax, -20);
+        const float inv_d = (float)NBK / (4.0f * sig);
+        auto dt = [&](T v) -> float { return fabsf(__fsub_rn((float)v, m32)); };
+        auto db = [&](float d) -> int {
+            const float f = fminf(__fmul_rn(d, inv_d), (float)(NBK - 1));
+            return __float_as_int(__fadd_rn(f, 12582912.0f)) - 0x4B400000;
+        };
+        if (nvalid > 0) {
+#pragma unroll
+            for (int r = 0; r < R2; ++r)
+                if (r < nvalid) atomicAdd(&sh.hist[db(dt(x[r]))], 1u);
+        }
+        __syncthreads();
+        blk_find2(sh, r1, r2);
+        // one extra bucket on each side (more if 3E spans buckets) holds every
+        // sample whose exact deviation can be the MAD
+        const int marg = 1 + (int)ceilf(3.0f * E * inv_d);
+        const int c1 = sh.bin_a - marg, c2 = sh.bin_b + marg;
+        uint32_t nbel = 0;
+        if (nvalid > 0) {
+#pragma unroll
+            for (int r = 0; r < R2; ++r)
+                if (r < nvalid) {
+                    const int b = db(dt(x[r]));
+                    if (b < c1) {
+                        ++nbel;
+                    } else if (b <= c2) {
+                        uint32_t s = atomicAdd(&sh.cnt, 1u);
+                        if (s < CAPM) sh.cand[s] = fabs((double)x[r] - med);
+                    }
+                }
+        }
+        nbel = __reduce_add_sync(0xffffffffu, nbel);
+        if (lane == 0 && nbel) atomicAdd(&sh.below, nbel);
+        __syncthreads();
+        const uint32_t cc = sh.cnt, cb = sh.below;
+        if (cc <= CAPM && cb <= r1 && r2 - cb < cc) {
+            double d1, d2;
+            cand_pick2(sh, cc, r1 - cb, r2 - cb, &d1, &d2);
+            mad = (r1 == r2) ? d1 : (d1 + d2) / 2;
+        } else {
+            if (cc <= CAPM) dev_fail(d_status, FFA_ERR_DEVICE);  // bracket invariant broken
+            const T* vb = buf;
+            auto key = [vb, med](int j) -> uint64_t { return dkey(fabs((double)vb[sidx(j)] - med)); };
+            const uint64_t k1 = smem_select64(sh, p0, r1, key);
+            const uint64_t k2 = (r1 == r2) ? k1 : smem_select64(sh, p0, r2, key);
+            const double d1 = dkey_inv(k1), d2 = dkey_inv(k2);
+            mad = (r1 == r2) ? d1 : (d1 + d2) / 2;
+        }
+        __syncthreads();
+    }
+
+    // ---- blocked cyclic prefix (bins past p0 repeat the profile) ----
+    // Extension blocks (index >= T2) start at bin 32768 > p0, above the value
+    // region of the buffer, so their prefixes are stored at once; own blocks
+    // overwrite values and wait until every thread has read its values.
+    const int eb2 = tid + T2;  // this thread's extension block, if any
+    T tot = 0, tot2 = 0;
+    if (eb2 < nbe) {
+#pragma unroll 4
+        for (int r = 0; r < R2; ++r) {
+            const T v = buf[sidx((eb2 * R2 + r) % p0)];
+            buf[sidx(eb2 * R2 + r)] = tot2;
+            tot2 = tot2 + v;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R2; ++r) {
+        const int j = base_pos + r;
+        T v = x[r];
+        if (j >= p0) v = (tid < nbe) ? buf[sidx(j % p0)] : (T)0;
+        x[r] = tot;  // exclusive in-block prefix
+        tot = tot + v;
+    }
+    __syncthreads();  // every value read: own blocks now take the prefixes
+    {
+        T* blk = buf + sidx(base_pos);
+#pragma unroll
+        for (int r = 0; r < R2; r += 4) *reinterpret_cast<int4*>(blk + r) = *reinterpret_cast<const int4*>(&x[r]);
+    }
+    if constexpr (Traits<T>::is_int) {
+        uint32_t t0, t1;
+        const uint32_t ex0 = blk_exscan_u((uint32_t)tot, sh, &t0);
+        int* cbi = reinterpret_cast<int*>(sh.cbh);
+        cbi[tid] = (int)ex0;
+        if (nbe > T2) {
+            const uint32_t ex1 = blk_exscan_u(eb2 < nbe ? (uint32_t)tot2 : 0u, sh, &t1);
+            if (eb2 <= MAXB) cbi[eb2] = (int)(t0 + ex1);
+        } else if (tid == 0) {
+            cbi[T2] = (int)t0;
+        }
+    } else {
+        float oh, ol, th, tl, oh2, ol2, th2, tl2;
+        blk_exscan_ff((float)tot, sh, oh, ol, th, tl);
+        sh.cbh[tid] = oh;
+        sh.cbl[tid] = ol;
+        if (nbe > T2) {
+            blk_exscan_ff(eb2 < nbe ? (float)tot2 : 0.0f, sh, oh2, ol2, th2, tl2);
+            if (eb2 <= MAXB) {
+                float h, l;
+                ff_add(th, tl, oh2, ol2, h, l);
+                sh.cbh[eb2] = h;
+                sh.cbl[eb2] = l;
+            }
+        } else if (tid == 0) {
+            sh.cbh[T2] = th;
+            sh.cbl[T2] = tl;
+        }
+    }
+    __syncthreads();
+
+    // ---- widths (Section 2.2.1): per-thread maxima, warp-reduced ----
+    const bool own = base_pos < p0;
+    int dummy = -1;
+    for (int wi = 0; wi < wd.n; ++wi) {
+        T m = B::lowest();
+        if (own) m = width_max<T, false>(x, sh, buf, tid, wd.w[wi], nvalid, (T)0, &dummy);
+        if constexpr (Traits<T>::is_int) {
+            m = warp_maxi(m);
+            if (lane == 0) sh.wredi[wi][warp] = m;
+        } else {
+            m = warp_max(m);
+            if (lane == 0) sh.wred[wi][warp] = m;
+        }
+    }
+    __syncthreads();
+    // S/N per width in FP64 (round-to-nearest intrinsics, no contraction), one
+    // width per lane of warp 0; best = max S/N, ties to the smaller width
+    if (warp == 0) {
+        double snr = -INFINITY;
+        if (lane < wd.n) {
+            double Bw;
+            if constexpr (Traits<T>::is_int) {
+                int mm = sh.wredi[lane][lane];
+                for (int q = 1; q < 32; ++q) mm = max(mm, sh.wredi[lane][(q + lane) & 31]);
+                Bw = (double)mm;
+            } else {
+                float mm = sh.wred[lane][lane];
+                for (int q = 1; q < 32; ++q) mm = fmaxf(mm, sh.wred[lane][(q + lane) & 31]);
+                Bw = (double)mm;
+            }
+            const double w = (double)wd.w[lane];
+            const double num = __dsub_rn(Bw, __dmul_rn(w, med));
+            const double den = __dmul_rn(__dmul_rn(KMAD, mad), __dsqrt_rn(w));
+            snr = __ddiv_rn(num, den);
+        }
+        int bw = lane;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double os = __shfl_xor_sync(0xffffffffu, snr, o);
+            const int ob = __shfl_xor_sync(0xffffffffu, bw, o);
+            if (os > snr || (os == snr && ob < bw)) {
+                snr = os;
+                bw = ob;
+            }
+        }
+        if (lane == 0) {
+            sh.dred[0] = snr;
+            sh.ired[0] = bw;
+        }
+    }
+    __syncthreads();
+    const double bestv = sh.dred[0];
+    const int bw = sh.ired[0];
+    __syncthreads();
+    // first argmax of the winning width, recomputed bit-identically
+    T target;
+    if constexpr (Traits<T>::is_int) target = (T)warp_maxi(sh.wredi[bw][lane]);
+    else target = (T)warp_max(sh.wred[bw][lane]);
+    int first = -1;
+    if (own && mad > 0.0) (void)width_max<T, true>(x, sh, buf, tid, wd.w[bw], nvalid, target, &first);
+    const int pos = blk_mini(first >= 0 ? base_pos + first : 0x7fffffff, sh);
+    if (tid == 0) {
+        ffa_record out;
+        if (!(mad > 0.0)) {
+            out.snr = 0.0f;
+            out.width = wd.w[0];
+            out.phase = 0;
+            out.flags = 1;
+        } else {
+            out.snr = __double2float_rn(bestv);
+            out.width = wd.w[bw];
+            out.phase = pos == 0x7fffffff ? 0 : pos;
+            out.flags = 0;
+            if (pos == 0x7fffffff) dev_fail(d_status, FFA_ERR_DEVICE);
+        }
+        rec[blockIdx.x] = out;
+    }
+}
+
+size_t score2_smem_bytes(int64_t p0, int wmax, size_t elem) {
+    int64_t nbe = (p0 + wmax + R2) / R2 + 1;
+    int64_t nbins = (nbe > T2 ? nbe : T2) * R2 + R2;
+    return ((sizeof(Sh2) + 15) & ~(size_t)15) + (size_t)(nbins + 4 * (nbins / 32) + 64) * elem;
+}
+
+ffa_status launch_score2(const void* d_prof, int32_t precision, bool fused, int64_t count,
+                         int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
+                         ffa_record* d_rec, int32_t* d_status, cudaStream_t st) {
+    if (count <= 0) return FFA_OK;
+    const int wmax = wd.w[wd.n - 1];
+    if (p0 < 1 || (p0 + wmax + R2) / R2 + 1 > MAXB || (p0 + R2 - 1) / R2 > T2)
+        return fail(FFA_ERR_UNSUPPORTED, "score: profile longer than 32768 bins");
+    size_t smem = score2_smem_bytes(p0, wmax, 4);
+    if (smem > 227 * 1024) return fail(FFA_ERR_UNSUPPORTED, "score: profile too long for shared memory");
+    ffa_status es;
+#define FFA_S2(TT, FF)                                                                       \
+    es = ensure_smem((const void*)k_score2<TT, FF>, smem);                                   \
+    if (es != FFA_OK) return es;                                                             \
+    k_score2<TT, FF><<<(unsigned)count, T2, smem, st>>>((const TT*)d_prof, p0, m_rows, trial0, \
+                                                        wd, d_rec, d_status);
+    if (precision == FFA_FOLD_F32) {
+        if (fused) { FFA_S2(float, true) } else { FFA_S2(float, false) }
+    } else {
+        if (fused) { FFA_S2(int32_t, true) } else { FFA_S2(int32_t, false) }
+    }
+#undef FFA_S2
+    FFA_LAUNCH_CHECK("k_score2");
+    count_launch();
+    return FFA_OK;
+}
+
+}  // namespace ffa

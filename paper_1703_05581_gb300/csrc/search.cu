@@ -479,13 +479,17 @@ ffa_status ffa_search(const ffa_plan* p, const void* d_series, void* d_ws, size_
         PhaseTimer fold_t(1, o, st);
         for (int64_t t = 0; t < p->oct_count[o]; ++t) {
             const ffa_plan_entry& e = p->entries[(size_t)(p->oct_first[o] + t)];
-            s = launch_fold(z, c.precision, e.p0, e.m_data, e.m_rows, plane0, plane1, st);
+            int m = 0;
+            while ((1 << m) < e.m_rows) ++m;
+            // all but the last stage; the scorer applies the last one while loading
+            s = launch_fold(z, c.precision, e.p0, e.m_data, e.m_rows, m > 0 ? m - 1 : 0, plane0,
+                            plane1, st);
             if (s != FFA_OK) return s;
             ScoreWidths wd;
             wd.n = e.n_widths;
             for (int k = 0; k < 16; ++k) wd.w[k] = e.widths[k];
-            s = launch_score(plane0, c.precision, e.m_rows, e.p0, wd, d_records + e.first_trial,
-                             d_status, st);
+            s = launch_score2(plane0, c.precision, true, e.m_rows, 0, e.p0, e.m_rows, wd,
+                              d_records + e.first_trial, d_status, st);
             if (s != FFA_OK) return s;
         }
         fold_t.stop();
@@ -640,7 +644,7 @@ ffa_status ffa_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_da
         return fail(FFA_ERR_ARG, "fold: need p0 >= 1, m_rows a power of two >= m_data");
     if (precision != FFA_FOLD_F32 && precision != FFA_FOLD_I8) return fail(FFA_ERR_ARG, "fold: bad precision");
     if (!d_z || !d_plane || !d_tmp) return fail(FFA_ERR_ARG, "fold: null buffer");
-    return launch_fold(d_z, precision, p0, m_data, m_rows, d_plane, d_tmp, as_stream(stream));
+    return launch_fold(d_z, precision, p0, m_data, m_rows, -1, d_plane, d_tmp, as_stream(stream));
 }
 
 ffa_status ffa_score(const void* d_profiles, int32_t precision, int64_t count, int64_t p0,
@@ -658,7 +662,8 @@ ffa_status ffa_score(const void* d_profiles, int32_t precision, int64_t count, i
     }
     if (count > 0 && (!d_profiles || !d_records)) return fail(FFA_ERR_ARG, "score: null buffer");
     if (precision != FFA_FOLD_F32 && precision != FFA_FOLD_I8) return fail(FFA_ERR_ARG, "score: bad precision");
-    return launch_score(d_profiles, precision, count, p0, wd, d_records, d_status, as_stream(stream));
+    return launch_score2(d_profiles, precision, false, count, 0, p0, 1, wd, d_records, d_status,
+                         as_stream(stream));
 }
 
 }  // extern "C"
