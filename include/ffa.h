@@ -181,6 +181,27 @@ ffa_status ffa_normalise(const double* d_resid, int64_t n, int32_t precision, vo
 ffa_status ffa_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
                     int64_t m_rows, void* d_plane, void* d_tmp, void* stream);
 
+/* Variant of ffa_fold that allocates nothing and takes no scratch argument.
+ * The paper has no counterpart: it serves callers that cannot allocate device
+ * memory at the point of the call -- for example a real-time pipeline that
+ * forbids allocator calls inside its processing loop, or a plug-in that is
+ * handed device buffers for its input and output but no allocator.  The
+ * scratch plane lives in a fixed file-scope device array of
+ * FFA_NOALLOC_FOLD_MAX_ELEMS 32-bit elements (32 MiB) that every GPU loading
+ * the library holds until the process exits.  Requires m_rows * p0 <=
+ * FFA_NOALLOC_FOLD_MAX_ELEMS, else FFA_ERR_UNSUPPORTED with a message.
+ * The first call on a device looks up the array's device address (a
+ * cudaGetSymbolAddress, once per device, with that device current); make that
+ * first call before any stream capture.  No cudaMalloc, cudaFree or other
+ * allocating routine is called.  All calls share the array and it keeps the
+ * last call's contents; nothing in it needs to start at zero because every
+ * element read has first been written by the same call.  Calls that overlap
+ * on the GPU (different streams, threads or processes sharing the context)
+ * race on the array: serialise them.  Results equal ffa_fold's bit for bit. */
+#define FFA_NOALLOC_FOLD_MAX_ELEMS (8 * 1024 * 1024)
+ffa_status ffa_fold_noalloc(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
+                            int64_t m_rows, void* d_plane, void* stream);
+
 /* Algorithm 1 (Section 2.2.1) on `count` profiles of p0 bins (float or
  * int32 per precision), widths given on the host; one record per profile. */
 ffa_status ffa_score(const void* d_profiles, int32_t precision, int64_t count, int64_t p0,

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -365,3 +367,45 @@ ffa_status launch_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m
 }
 
 }  // namespace ffa
+
+// ---------------------------------------------------------------------------
+// Fold without any allocation (see ffa_fold_noalloc in include/ffa.h).
+// ---------------------------------------------------------------------------
+namespace {
+// Scratch plane shared by every ffa_fold_noalloc call on a device; it lives
+// in the module image, so every GPU that loads the library holds it.
+static __device__ __align__(256) float g_fold_scratch[FFA_NOALLOC_FOLD_MAX_ELEMS];
+
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[64] = {};
+}  // namespace
+
+extern "C" ffa_status ffa_fold_noalloc(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
+                                       int64_t m_rows, void* d_plane, void* stream) {
+    using namespace ffa;
+    if (p0 < 1 || m_data < 0 || m_rows < 1 || (m_rows & (m_rows - 1)) != 0 || m_data > m_rows)
+        return fail(FFA_ERR_ARG, "fold_noalloc: need p0 >= 1, m_rows a power of two >= m_data");
+    if (precision != FFA_FOLD_F32 && precision != FFA_FOLD_I8)
+        return fail(FFA_ERR_ARG, "fold_noalloc: bad precision");
+    if (!d_z || !d_plane) return fail(FFA_ERR_ARG, "fold_noalloc: null buffer");
+    if (m_rows * p0 > (int64_t)FFA_NOALLOC_FOLD_MAX_ELEMS)
+        return fail(FFA_ERR_UNSUPPORTED,
+                    "fold_noalloc: m_rows * p0 exceeds FFA_NOALLOC_FOLD_MAX_ELEMS (the fixed scratch)");
+    int dev = 0;
+    FFA_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(FFA_ERR_UNSUPPORTED, "fold_noalloc: device index >= 64");
+    void* scratch;
+    {
+        // set-up once per device, with that device current: the device address of
+        // the array (its host-side name is only a stand-in, not a device address)
+        std::lock_guard<std::mutex> lk(g_scratch_mu);
+        if (!g_scratch_ptr[dev]) {
+            void* ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_fold_scratch);
+            if (e != cudaSuccess || !ptr) return cuda_fail(e, "fold_noalloc: cudaGetSymbolAddress");
+            g_scratch_ptr[dev] = ptr;
+        }
+        scratch = g_scratch_ptr[dev];
+    }
+    return launch_fold(d_z, precision, p0, m_data, m_rows, -1, d_plane, scratch, as_stream(stream));
+}

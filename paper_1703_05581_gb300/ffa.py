@@ -25,6 +25,7 @@ OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_CANCELLED, ERR_UNSUPPORTED, ERR
 IN_F32, IN_U8, IN_F64 = 0, 1, 2
 FOLD_F32, FOLD_I8 = 0, 1
 STATS_DOUBLES = 1026
+NOALLOC_FOLD_MAX_ELEMS = 8 * 1024 * 1024
 
 
 class FFAError(RuntimeError):
@@ -83,6 +84,7 @@ _sig = {
     "ffa_detrend": ([_P, _i64, _i32, _P, _P, _P], C.c_int),
     "ffa_normalise": ([_P, _i64, _i32, _P, _P, _P], C.c_int),
     "ffa_fold": ([_P, _i32, _i64, _i64, _i64, _P, _P, _P], C.c_int),
+    "ffa_fold_noalloc": ([_P, _i32, _i64, _i64, _i64, _P, _P], C.c_int),
     "ffa_score": ([_P, _i32, _i64, _i64, _P, _i32, _P, _P, _P], C.c_int),
     "ffa_timing_enable": ([_i32], C.c_int),
     "ffa_launch_count": ([], C.c_int64),
