@@ -53,7 +53,9 @@ __device__ __forceinline__ int sidx(int t) { return t + 4 * (t >> 5); }
 
 struct Sh2 {
     uint32_t hist[NBK];
-    double cand[CAPM];
+    unsigned long long cand[CAPM];  // order-preserving keys of the candidates
+    float candf[CAPM];    // gathered values; FP64 is applied per candidate afterwards
+    double bw_max[16];    // per-width block maxima
     float cbh[MAXB + 1];  // block offsets (hi) / int offsets reinterpreted
     float cbl[MAXB + 1];  // block offsets (lo)
     float wred[16][32];   // per-width warp maxima (float profiles)
@@ -61,6 +63,8 @@ struct Sh2 {
     float fred[32];
     double dred[64];
     int ired[32];
+    int ired2[CAPM];      // gathered int values
+    unsigned long long ukey[2];
     uint32_t cnt, below;
     int bin_a, bin_b;
     uint32_t below_a, below_b;
@@ -85,14 +89,6 @@ __device__ __forceinline__ int warp_mini(int v) {
     return v;
 }
 
-__device__ float blk_sum(float v, Sh2& sh) {
-    v = warp_sum(v);
-    if ((threadIdx.x & 31) == 0) sh.fred[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float r = warp_sum(sh.fred[threadIdx.x & 31]);
-    __syncthreads();
-    return r;
-}
 // block sums of a and b and the max of c (one barrier pair)
 __device__ void blk_stats(float& a, float& b, float& c, Sh2& sh) {
     a = warp_sum(a);
@@ -109,14 +105,6 @@ __device__ void blk_stats(float& a, float& b, float& c, Sh2& sh) {
     b = warp_sum(sh.wred[0][l]);
     c = warp_max(sh.wred[1][l]);
     __syncthreads();
-}
-__device__ float blk_max(float v, Sh2& sh) {
-    v = warp_max(v);
-    if ((threadIdx.x & 31) == 0) sh.fred[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float r = warp_max(sh.fred[threadIdx.x & 31]);
-    __syncthreads();
-    return r;
 }
 __device__ int blk_mini(int v, Sh2& sh) {
     v = warp_mini(v);
@@ -242,20 +230,22 @@ __device__ void blk_find(Sh2& sh, uint32_t rank, int* bin, uint32_t* below) {
     __syncthreads();
 }
 
-// Values of ranks ta <= tb among sh.cand[0..n) (ties broken by index): the
-// n x n comparisons are spread over the whole CTA, each candidate's rank is
-// accumulated in shared memory (sh.hist is free at this point).
-__device__ void cand_pick2(Sh2& sh, uint32_t n, uint32_t ta, uint32_t tb, double* va, double* vb) {
+// Keys of ranks ta <= tb among the keys sh.cand[0..n) (ties broken by index):
+// the n x n integer comparisons are spread over the whole CTA and each
+// candidate's rank is accumulated in shared memory (sh.hist is free here).
+// Integer keys, not doubles: FP64 compares are slow on this part.
+__device__ void cand_pick2(Sh2& sh, uint32_t n, uint32_t ta, uint32_t tb, unsigned long long* ka,
+                           unsigned long long* kb) {
     for (uint32_t i = threadIdx.x; i < n; i += T2) sh.hist[i] = 0;
     __syncthreads();
     const uint32_t chunks = (T2 + n - 1) / (n ? n : 1);  // threads per candidate
     const uint32_t pairs = n * chunks;
     for (uint32_t p = threadIdx.x; p < pairs; p += T2) {
         const uint32_t i = p % n, part = p / n;
-        const double ci = sh.cand[i];
+        const unsigned long long ci = sh.cand[i];
         uint32_t rk = 0;
         for (uint32_t j = part; j < n; j += chunks) {
-            const double cj = sh.cand[j];
+            const unsigned long long cj = sh.cand[j];
             rk += (cj < ci) || (cj == ci && j < i);
         }
         if (rk) atomicAdd(&sh.hist[i], rk);
@@ -263,12 +253,12 @@ __device__ void cand_pick2(Sh2& sh, uint32_t n, uint32_t ta, uint32_t tb, double
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < n; i += T2) {
         const uint32_t rk = sh.hist[i];
-        if (rk == ta) sh.dred[1] = sh.cand[i];
-        if (rk == tb) sh.dred[2] = sh.cand[i];
+        if (rk == ta) sh.ukey[0] = sh.cand[i];
+        if (rk == tb) sh.ukey[1] = sh.cand[i];
     }
     __syncthreads();
-    *va = sh.dred[1];
-    *vb = sh.dred[2];
+    *ka = sh.ukey[0];
+    *kb = sh.ukey[1];
     __syncthreads();
 }
 
@@ -563,7 +553,10 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
                 int b = bucket_m(x[r]);
                 if (b >= mb1 && b <= mb2) {
                     uint32_t s = atomicAdd(&sh.cnt, 1u);
-                    if (s < CAPM) sh.cand[s] = (double)x[r];
+                    if (s < CAPM) {
+                        if constexpr (Traits<T>::is_int) sh.ired2[s] = (int)x[r];
+                        else sh.candf[s] = (float)x[r];
+                    }
                 }
             }
     }
@@ -571,9 +564,22 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
     double med;
     {
         const uint32_t cc = sh.cnt;
+        for (uint32_t i = tid; i < cc && i < CAPM; i += T2) {
+            if constexpr (Traits<T>::is_int) sh.cand[i] = ikey(sh.ired2[i]);
+            else sh.cand[i] = fkey(sh.candf[i]);
+        }
+        __syncthreads();
         if (cc <= CAPM) {
+            unsigned long long ka, kb;
+            cand_pick2(sh, cc, r1 - mbelow, r2 - mbelow, &ka, &kb);
             double a, b;
-            cand_pick2(sh, cc, r1 - mbelow, r2 - mbelow, &a, &b);
+            if constexpr (Traits<T>::is_int) {
+                a = (double)(int32_t)((uint32_t)ka ^ 0x80000000u);
+                b = (double)(int32_t)((uint32_t)kb ^ 0x80000000u);
+            } else {
+                a = (double)fkey_inv((uint32_t)ka);
+                b = (double)fkey_inv((uint32_t)kb);
+            }
             med = (r1 == r2) ? a : (a + b) / 2;
         } else {
             const T* vb = buf;
@@ -635,15 +641,16 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
                     const int b = eb(e);
                     if (b >= c1 && b <= c2) {
                         uint32_t s = atomicAdd(&sh.cnt, 1u);
-                        if (s < CAPM) sh.cand[s] = (double)e;
+                        if (s < CAPM) sh.cand[s] = (unsigned long long)(uint32_t)e;
                     }
                 }
         }
         __syncthreads();
         const uint32_t cc = sh.cnt;
         if (cc <= CAPM) {
-            double e1, e2;
-            cand_pick2(sh, cc, r1 - cbel, r2 - cbel, &e1, &e2);
+            unsigned long long k1, k2;
+            cand_pick2(sh, cc, r1 - cbel, r2 - cbel, &k1, &k2);
+            const double e1 = (double)k1, e2 = (double)k2;
             mad = (r1 == r2) ? e1 / 2 : (e1 + e2) / 4;
         } else {
             const T* vb = buf;
@@ -686,7 +693,7 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
                         ++nbel;
                     } else if (b <= c2) {
                         uint32_t s = atomicAdd(&sh.cnt, 1u);
-                        if (s < CAPM) sh.cand[s] = fabs((double)x[r] - med);
+                        if (s < CAPM) sh.candf[s] = (float)x[r];
                     }
                 }
         }
@@ -694,9 +701,12 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
         if (lane == 0 && nbel) atomicAdd(&sh.below, nbel);
         __syncthreads();
         const uint32_t cc = sh.cnt, cb = sh.below;
+        for (uint32_t i = tid; i < cc && i < CAPM; i += T2) sh.cand[i] = dkey(fabs((double)sh.candf[i] - med));
+        __syncthreads();
         if (cc <= CAPM && cb <= r1 && r2 - cb < cc) {
-            double d1, d2;
-            cand_pick2(sh, cc, r1 - cb, r2 - cb, &d1, &d2);
+            unsigned long long k1, k2;
+            cand_pick2(sh, cc, r1 - cb, r2 - cb, &k1, &k2);
+            const double d1 = dkey_inv(k1), d2 = dkey_inv(k2);
             mad = (r1 == r2) ? d1 : (d1 + d2) / 2;
         } else {
             if (cc <= CAPM) dev_fail(d_status, FFA_ERR_DEVICE);  // bracket invariant broken
@@ -716,10 +726,12 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
     // overwrite values and wait until every thread has read its values.
     const int eb2 = tid + T2;  // this thread's extension block, if any
     T tot = 0, tot2 = 0;
+    const bool one_wrap = nbe * R2 <= 2 * p0;  // extension bins map to j - p0
     if (eb2 < nbe) {
 #pragma unroll 4
         for (int r = 0; r < R2; ++r) {
-            const T v = buf[sidx((eb2 * R2 + r) % p0)];
+            const int j = eb2 * R2 + r;
+            const T v = buf[sidx(one_wrap ? j - p0 : j % p0)];
             buf[sidx(eb2 * R2 + r)] = tot2;
             tot2 = tot2 + v;
         }
@@ -728,7 +740,7 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
     for (int r = 0; r < R2; ++r) {
         const int j = base_pos + r;
         T v = x[r];
-        if (j >= p0) v = (tid < nbe) ? buf[sidx(j % p0)] : (T)0;
+        if (j >= p0) v = (tid < nbe) ? buf[sidx(one_wrap ? j - p0 : j % p0)] : (T)0;
         x[r] = tot;  // exclusive in-block prefix
         tot = tot + v;
     }
@@ -784,37 +796,44 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
         }
     }
     __syncthreads();
-    // S/N per width in FP64 (round-to-nearest intrinsics, no contraction), one
-    // width per lane of warp 0; best = max S/N, ties to the smaller width
+    // per-width block maxima: warp w reduces width w's 32 warp maxima
+    if (warp < wd.n) {
+        double Bw;
+        if constexpr (Traits<T>::is_int) Bw = (double)warp_maxi(sh.wredi[warp][lane]);
+        else Bw = (double)warp_max(sh.wred[warp][lane]);
+        if (lane == 0) sh.bw_max[warp] = Bw;
+    }
+    __syncthreads();
+    // S/N_w = (B_w - w*med) / (K*MAD*sqrt(w)) in FP64.  Widths are ranked with
+    // one shared reciprocal (within a few ulp of the quotient); the winner's
+    // S/N is then the correctly rounded quotient (round-to-nearest intrinsics,
+    // no contraction).  Ties go to the smaller width.
     if (warp == 0) {
-        double snr = -INFINITY;
+        const double kmad = __dmul_rn(KMAD, mad);
+        const double rk = __drcp_rn(kmad);
+        double key = -INFINITY;
         if (lane < wd.n) {
-            double Bw;
-            if constexpr (Traits<T>::is_int) {
-                int mm = sh.wredi[lane][lane];
-                for (int q = 1; q < 32; ++q) mm = max(mm, sh.wredi[lane][(q + lane) & 31]);
-                Bw = (double)mm;
-            } else {
-                float mm = sh.wred[lane][lane];
-                for (int q = 1; q < 32; ++q) mm = fmaxf(mm, sh.wred[lane][(q + lane) & 31]);
-                Bw = (double)mm;
-            }
             const double w = (double)wd.w[lane];
-            const double num = __dsub_rn(Bw, __dmul_rn(w, med));
-            const double den = __dmul_rn(__dmul_rn(KMAD, mad), __dsqrt_rn(w));
-            snr = __ddiv_rn(num, den);
+            const double num = __dsub_rn(sh.bw_max[lane], __dmul_rn(w, med));
+            // 1/sqrt(w) for w = 2^n: 2^(-n/2) exactly for even n, else 2^(-(n-1)/2)/sqrt(2)
+            const int n = __ffs(wd.w[lane]) - 1;
+            const double rs = (n & 1) ? ldexp(0.70710678118654752440, -(n - 1) / 2) : ldexp(1.0, -n / 2);
+            key = __dmul_rn(__dmul_rn(num, rk), rs);
         }
         int bw = lane;
         for (int o = 16; o > 0; o >>= 1) {
-            const double os = __shfl_xor_sync(0xffffffffu, snr, o);
+            const double ok = __shfl_xor_sync(0xffffffffu, key, o);
             const int ob = __shfl_xor_sync(0xffffffffu, bw, o);
-            if (os > snr || (os == snr && ob < bw)) {
-                snr = os;
+            if (ok > key || (ok == key && ob < bw)) {
+                key = ok;
                 bw = ob;
             }
         }
         if (lane == 0) {
-            sh.dred[0] = snr;
+            const double w = (double)wd.w[bw];
+            const double num = __dsub_rn(sh.bw_max[bw], __dmul_rn(w, med));
+            const double den = __dmul_rn(kmad, __dsqrt_rn(w));
+            sh.dred[0] = __ddiv_rn(num, den);
             sh.ired[0] = bw;
         }
     }
