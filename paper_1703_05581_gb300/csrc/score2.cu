@@ -441,11 +441,12 @@ __device__ __forceinline__ T width_max(const T (&c)[R2], const Sh2& sh, const T*
 }
 
 // prof: FUSED ? the stage-(m-1) plane (m_rows rows of p0) : profiles of p0.
-// Record blockIdx.x belongs to trial trial0 + blockIdx.x.
+// Record i belongs to trial trial0 + i, i < count.
 template <class T, bool FUSED>
 __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, int64_t p0_,
-                                                  int64_t m_rows, int64_t trial0, ScoreWidths wd,
-                                                  ffa_record* __restrict__ rec, int32_t* d_status) {
+                                                  int64_t m_rows, int64_t trial0, int64_t count,
+                                                  ScoreWidths wd, ffa_record* __restrict__ rec,
+                                                  int32_t* d_status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sh2& sh = *reinterpret_cast<Sh2*>(smem_raw);
     T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(Sh2) + 15) & ~(size_t)15));
@@ -453,9 +454,24 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
     const int p0 = (int)p0_;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int64_t k = trial0 + blockIdx.x;
     const int wmax = wd.w[wd.n - 1];
     const int nbe = (p0 + wmax + R2) / R2 + 1;  // blocks incl. the cyclic extension
+    // persistent: this CTA scores trials it, it + gridDim.x, ...
+    for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+    const int64_t k = trial0 + it;
+    {
+        // pull the next trial's rows towards L2 while this one is scored
+        const int64_t kn = k + gridDim.x;
+        if (it + gridDim.x < count) {
+            const T* nh = FUSED ? (m_rows > 1 ? prof + (kn >> 1) * p0_ : prof) : prof + kn * p0_;
+            const T* nt = (FUSED && m_rows > 1) ? prof + ((m_rows >> 1) + (kn >> 1)) * p0_ : nullptr;
+            const int lines = (int)((p0_ * (int64_t)sizeof(T) + 127) / 128);
+            for (int l = tid; l < lines; l += T2) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nh + l * (128 / sizeof(T))));
+                if (nt) asm volatile("prefetch.global.L2 [%0];" ::"l"(nt + l * (128 / sizeof(T))));
+            }
+        }
+    }
 
     // ---- load; fused last FFA stage: head row k>>1 plus tail row M/2 + (k>>1)
     // read ceil(k/2) bins further on
@@ -810,19 +826,19 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
     // no contraction).  Ties go to the smaller width.
     if (warp == 0) {
         const double kmad = __dmul_rn(KMAD, mad);
-        const double rk = __drcp_rn(kmad);
-        double key = -INFINITY;
+        // ranking key (FP32): numerator formed in FP64 then scaled by 1/sqrt(w)
+        float key = -INFINITY;
         if (lane < wd.n) {
             const double w = (double)wd.w[lane];
             const double num = __dsub_rn(sh.bw_max[lane], __dmul_rn(w, med));
-            // 1/sqrt(w) for w = 2^n: 2^(-n/2) exactly for even n, else 2^(-(n-1)/2)/sqrt(2)
             const int n = __ffs(wd.w[lane]) - 1;
-            const double rs = (n & 1) ? ldexp(0.70710678118654752440, -(n - 1) / 2) : ldexp(1.0, -n / 2);
-            key = __dmul_rn(__dmul_rn(num, rk), rs);
+            // 1/sqrt(w) for w = 2^n: 2^(-n/2) for even n, else 2^(-(n-1)/2)/sqrt(2)
+            const float rs = (n & 1) ? ldexpf(0.70710678f, -(n - 1) / 2) : ldexpf(1.0f, -n / 2);
+            key = __double2float_rn(num) * rs;
         }
         int bw = lane;
         for (int o = 16; o > 0; o >>= 1) {
-            const double ok = __shfl_xor_sync(0xffffffffu, key, o);
+            const float ok = __shfl_xor_sync(0xffffffffu, key, o);
             const int ob = __shfl_xor_sync(0xffffffffu, bw, o);
             if (ok > key || (ok == key && ob < bw)) {
                 key = ok;
@@ -862,8 +878,10 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
             out.flags = 0;
             if (pos == 0x7fffffff) dev_fail(d_status, FFA_ERR_DEVICE);
         }
-        rec[blockIdx.x] = out;
+        rec[it] = out;
     }
+    __syncthreads();
+    }  // trials
 }
 
 size_t score2_smem_bytes(int64_t p0, int wmax, size_t elem) {
@@ -881,12 +899,16 @@ ffa_status launch_score2(const void* d_prof, int32_t precision, bool fused, int6
         return fail(FFA_ERR_UNSUPPORTED, "score: profile longer than 32768 bins");
     size_t smem = score2_smem_bytes(p0, wmax, 4);
     if (smem > 227 * 1024) return fail(FFA_ERR_UNSUPPORTED, "score: profile too long for shared memory");
+    int dev = 0, nsm = 0;
+    FFA_CUDA_TRY(cudaGetDevice(&dev));
+    FFA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)(count < nsm ? count : nsm);  // one resident CTA per SM
     ffa_status es;
 #define FFA_S2(TT, FF)                                                                       \
     es = ensure_smem((const void*)k_score2<TT, FF>, smem);                                   \
     if (es != FFA_OK) return es;                                                             \
-    k_score2<TT, FF><<<(unsigned)count, T2, smem, st>>>((const TT*)d_prof, p0, m_rows, trial0, \
-                                                        wd, d_rec, d_status);
+    k_score2<TT, FF><<<grid, T2, smem, st>>>((const TT*)d_prof, p0, m_rows, trial0, count, wd, \
+                                             d_rec, d_status);
     if (precision == FFA_FOLD_F32) {
         if (fused) { FFA_S2(float, true) } else { FFA_S2(float, false) }
     } else {
