@@ -90,6 +90,31 @@ def fold_score_bytes(entries, in_bytes: int = 4) -> np.ndarray:
     return out
 
 
+# GB300 FP32/INT32 lane peak for ALU-bound kernels: 152 SMs x 128 lanes x 2070 MHz
+# (the maximum SM clock); one algorithmic operation per lane per clock.
+ALU_LANES = 152 * 128
+ALU_MAX_MHZ = 2070.0
+# DRAM bytes per profile bin of one k_score2 launch (read + write), from the
+# ncu capture summarised in profiles/k_score2_p0_20000_m4096.md:
+# (329.27 MB + 11.71 MB) / (4096 * 20000).  Set to None when the kernel changes.
+SCORE_DRAM_BYTES_PER_ELEM = (329268480 + 11707904) / (4096 * 20000)
+
+
+def score_ops(entries) -> np.ndarray:
+    """Algorithmic operations of one scoring launch (a base period's M trials):
+    per bin, the fused last FFA stage's add, per width a box add and a max,
+    one deviation |x - median|, and at least one comparison per bin for each of
+    the two order-statistic selections (median, MAD)."""
+    e = entries
+    return e["m_rows"].astype(np.float64) * e["p0"] * (1.0 + 2.0 * e["n_widths"] + 3.0)
+
+
+def sampled(entries, octave, sample):
+    """Entries whose launches the library times: every sample-th of the octave."""
+    idx = np.flatnonzero(entries["octave"] == octave)
+    return entries[idx[::sample]]
+
+
 def measured_peaks():
     if os.path.exists(PEAKS_PATH):
         with open(PEAKS_PATH) as f:
@@ -330,14 +355,30 @@ def run_gpu(args):
         value = units * world * args.steps / (ms_max / 1e3)
         e2e_value = units * world * args.e2e_steps / e2e_s
         peak, peak_kind = measured_peaks()
-        # dominant kernel group: fold + Algorithm 1 scoring of an octave's base periods
+        # fold + score phase: HBM view (algorithmic bytes of the search's fold+score)
         fs_ms = phase_ms[1]
         fs_cnt = np.maximum(phase_cnt[1], 1)
         oct_ms = fs_ms / fs_cnt
         tot_bytes = float(np.sum(fs_bytes[: len(oct_ms)] * (phase_cnt[1] > 0)))
         tot_ms = float(np.sum(oct_ms * (phase_cnt[1] > 0)))
-        achieved = tot_bytes / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else 0.0
+        hbm_achieved = tot_bytes / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else 0.0
         prep_ms = float(np.sum(phase_ms[0] / np.maximum(phase_cnt[0], 1)))
+        # dominant kernel: k_score2, timed per launch on sampled base periods
+        sc_ops = sc_ms = sc_elems = sc_n = fo_ms = 0.0
+        for o in range(plan.n_octaves):
+            if phase_cnt[3][o] == 0:
+                continue
+            sub = sampled(plan.entries, o, ffa.TIMING_SAMPLE)
+            reps = phase_cnt[3][o] / max(len(sub), 1)  # timed steps
+            sc_ops += float(score_ops(sub).sum()) * reps
+            sc_elems += float((sub["m_rows"].astype(np.float64) * sub["p0"]).sum()) * reps
+            sc_ms += float(phase_ms[3][o])
+            fo_ms += float(phase_ms[2][o])
+            sc_n += float(phase_cnt[3][o])
+        alu_peak = ALU_LANES * ALU_MAX_MHZ * 1e6 / 1e12
+        alu_achieved = sc_ops / (sc_ms / 1e3) / 1e12 if sc_ms > 0 else 0.0
+        traffic = (SCORE_DRAM_BYTES_PER_ELEM * sc_elems / sc_n
+                   if SCORE_DRAM_BYTES_PER_ELEM and sc_n else None)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -345,10 +386,17 @@ def run_gpu(args):
             "config": dict(desc, l2="inputs and fold planes larger than L2 (no flush needed)",
                            trials=int(plan.n_trials), base_periods=int(plan.n_periods),
                            samples_x_trials=units),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "fold + Algorithm 1 scoring (per octave, all base periods)",
-                         "peak_kind": peak_kind,
+            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": alu_achieved / alu_peak, "traffic": traffic,
+                         "kernel": "k_score2 (Algorithm 1 + fused last FFA stage), mean over "
+                                   f"{int(sc_n)} sampled launches",
+                         "ops": "per bin: last-stage add + 2 per width + 3 (selections, deviation)",
+                         "peak_from": "152 SMs x 128 FP32/INT32 lanes x 2070 MHz",
+                         "score_ms_per_launch": sc_ms / max(sc_n, 1),
+                         "fold_ms_per_launch": fo_ms / max(sc_n, 1),
+                         "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": peak, "peak_kind": peak_kind,
+                                 "frac": hbm_achieved / peak,
+                                 "bytes": "algorithmic: 4*M_data*P0 + 16*M per base period"},
                          "phase_ms_per_step": {"prep": prep_ms, "fold_score": tot_ms}},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n,

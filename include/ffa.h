@@ -73,7 +73,16 @@ typedef struct {
     int32_t precision;       /* ffa_fold_precision                               */
     int32_t n_widths_fixed;  /* > 0: use widths_fixed[0..n) instead of duty_max  */
     int32_t widths_fixed[16];
+    int32_t scorer;          /* ffa_scorer: Algorithm 1 (default) or 2           */
+    float alg2_window;       /* Algorithm 2 exclusion window as a fraction of the
+                                profile (0 = the paper's 20 %)                     */
 } ffa_search_config;
+
+/* Profile scorer (Section 2.2): Algorithm 1, MAD-normalised boxcars; or
+ * Algorithm 2, boxcar then S/N against the off-pulse mean and standard
+ * deviation outside a window around the maximum (Eq. 5).  Algorithm 2's
+ * fixed-width "Ref" form is a single fixed width. */
+typedef enum { FFA_SCORE_ALG1 = 0, FFA_SCORE_ALG2 = 1 } ffa_scorer;
 
 /* One periodogram record per trial period (16 bytes).  flags bit 0: the
  * profile's MAD was zero (S/N reported as 0). */
@@ -137,6 +146,23 @@ ffa_status ffa_search(const ffa_plan* plan, const void* d_series, void* d_worksp
                       size_t workspace_bytes, ffa_record* d_records, int32_t* d_status,
                       void* stream);
 
+/* The same pipeline restricted to plan entries [entry_begin, entry_end)
+ * (base periods in periodogram order): octaves holding them are prepared,
+ * only those base periods are folded and scored, only their records are
+ * written.  Independent ranges may run on different devices or processes;
+ * their candidate lists merge on the host (the only exchange). */
+ffa_status ffa_search_entries(const ffa_plan* plan, const void* d_series, int64_t entry_begin,
+                              int64_t entry_end, void* d_workspace, size_t workspace_bytes,
+                              ffa_record* d_records, int32_t* d_status, void* stream);
+
+/* A batch of series (e.g. dedispersion trials of uneven length), each with
+ * its own plan: series i is searched with plans[i] into d_records[i] (host
+ * arrays of `count` pointers).  One workspace, at least the largest plan's
+ * workspace_bytes, serves every series in turn on `stream`. */
+ffa_status ffa_search_batch(const ffa_plan* const* plans, const void* const* d_series, int32_t count,
+                            void* d_workspace, size_t workspace_bytes, ffa_record* const* d_records,
+                            int32_t* d_status, void* stream);
+
 /* Candidate extraction (the first step of ffa2best, Section 2.3.3): records
  * with S/N >= snr_min, highest first (ties: lower periodogram index first),
  * at most top_k (<= 4096) of them, written to host memory `out`; *n_out
@@ -148,6 +174,15 @@ ffa_status ffa_candidates(const ffa_plan* plan, const ffa_record* d_records, dou
                           int32_t top_k, void* d_workspace, size_t workspace_bytes,
                           ffa_candidate* out, int32_t* n_out, int64_t* best,
                           int32_t* d_status, void* stream, int32_t timeout_ms);
+
+/* ffa_candidates over the trials of plan entries [entry_begin, entry_end)
+ * only (d_records is the full periodogram; other records are not read).
+ * Trial indices in `out` and *best are periodogram indices. */
+ffa_status ffa_candidates_entries(const ffa_plan* plan, int64_t entry_begin, int64_t entry_end,
+                                  const ffa_record* d_records, double snr_min, int32_t top_k,
+                                  void* d_workspace, size_t workspace_bytes, ffa_candidate* out,
+                                  int32_t* n_out, int64_t* best, int32_t* d_status, void* stream,
+                                  int32_t timeout_ms);
 
 /* Wait for `stream` with a bounded wait (polling), then read *d_status.
  * Returns FFA_ERR_TIMEOUT, FFA_ERR_CUDA, the device status, or FFA_OK. */
@@ -211,18 +246,28 @@ ffa_status ffa_score(const void* d_profiles, int32_t precision, int64_t count, i
 /* ---- timing (benchmark instrumentation) ---------------------------------------- */
 
 /* When enabled (process-wide), ffa_search records CUDA events on its stream
- * around two phases of every octave: 0 = series preparation (downsampling,
- * dereddening, normalisation) and 1 = fold + score of all base periods.
- * ffa_timing_read waits for the recorded events, writes the summed
- * milliseconds of phase p, octave o to ms[p * 64 + o] (cap >= 128 doubles)
- * and the number of recorded intervals to counts[p * 64 + o], then clears
- * the record.  Adds two event records per phase and octave; off by default. */
+ * around phases of every octave: 0 = series preparation (downsampling,
+ * dereddening, normalisation), 1 = fold + score of all base periods, and,
+ * for every 64th base period of the octave (entries first + 64 j), 2 = its
+ * fold launches and 3 = its scoring launch.  ffa_timing_read waits for the
+ * recorded events, writes the summed milliseconds of phase p, octave o to
+ * ms[p * 64 + o] (cap >= 256 doubles) and the number of recorded intervals
+ * to counts[p * 64 + o], then clears the record.  Off by default. */
 ffa_status ffa_timing_enable(int32_t on);
 
 /* Number of kernel launches (and device copies) the library has enqueued in
  * this process so far, all devices and threads together. */
 int64_t ffa_launch_count(void);
 ffa_status ffa_timing_read(double* ms, int32_t* counts, int32_t cap);
+
+/* Algorithm 2 (Section 2.2.2, Eq. 5) on `count` profiles of p0 bins: per
+ * width w the boxcar maximum I_max (first position j*), then I_av and the
+ * population standard deviation of the filtered bins farther than
+ * floor(excl_frac * p0 / 2) bins (cyclically) from j*, A = (I_max - I_av) /
+ * sigma; the record keeps the best width (ties: smaller), its j* and A. */
+ffa_status ffa_score_alg2(const void* d_profiles, int32_t precision, int64_t count, int64_t p0,
+                          const int32_t* widths, int32_t n_widths, float excl_frac,
+                          ffa_record* d_records, void* stream);
 
 /* ---- errors ------------------------------------------------------------------ */
 const char* ffa_status_string(ffa_status s);

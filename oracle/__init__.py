@@ -12,6 +12,7 @@ numpy arrays through ctypes.  Functions follow the paper:
 * ``normalise``             -- FP64 mean / population-std normalisation (+ int8 code)
 * ``fold`` / ``fold_trial`` -- Section 2.1 FFA recursion (Eq. 1-2, padding rule)
 * ``score_alg1``            -- Section 2.2.1 Algorithm 1 (Eq. 3-4)
+* ``score_alg2``            -- Section 2.2.2 Algorithm 2 (Eq. 5), with its fixed-width "Ref" form
 * ``plan`` / ``search`` / ``best`` -- the whole search, ffancy-style
 
 Parity is pinned by ``tests/test_oracle_*.py`` against brute force, closed
@@ -116,6 +117,7 @@ def lib():
                 getattr(L, name).argtypes = [P, i64, i64, i64, i64, P]
             for name in ("oracle_score_alg1_f64", "oracle_score_alg1_i64"):
                 getattr(L, name).argtypes = [P, i64, P, C.c_int32, P]
+            L.oracle_score_alg2_f64.argtypes = [P, i64, P, C.c_int32, C.c_double, P]
             L.oracle_plan.argtypes = [P, i64, P, i64, P, P]
             L.oracle_plan.restype = i64
             L.oracle_octave_series.argtypes = [P, P, i64, C.c_int, P, P, P, P, C.c_int]
@@ -201,6 +203,15 @@ def score_alg1(profile: np.ndarray, widths) -> np.ndarray:
     else:
         x = np.ascontiguousarray(profile, np.float64)
         lib().oracle_score_alg1_f64(_p(x), x.size, _p(w), w.size, _p(rec))
+    return rec[0]
+
+
+def score_alg2(profile: np.ndarray, widths, excl_frac: float = 0.2) -> np.ndarray:
+    """Algorithm 2 (Section 2.2.2, Eq. 5) on one profile; median/mad fields hold I_av/sigma."""
+    w = np.ascontiguousarray(widths, np.int32)
+    rec = np.zeros(1, SCORE_DTYPE)
+    x = np.ascontiguousarray(profile, np.float64)
+    lib().oracle_score_alg2_f64(_p(x), x.size, _p(w), w.size, float(excl_frac), _p(rec))
     return rec[0]
 
 

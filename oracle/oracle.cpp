@@ -37,7 +37,16 @@
 //   R12 int8 path: q = clip(rint(16 z), -127, 127), round half to even;
 //   R13 ties: within a trial max S/N, then smallest width, then smallest
 //      phase; across trials the first in (octave, P0, trial) order;
-//   R14 a base period with fewer than min_rows data rows is skipped.
+//   R14 a base period with fewer than min_rows data rows is skipped;
+//   R15 Algorithm 2 filters first: b_w[j] = sum_{i<w} x[(j+i) mod p0], not
+//      normalised; I_max = its maximum (first position j* on ties);
+//   R16 the Algorithm 2 exclusion window is the 2h+1 filtered bins within
+//      cyclic distance h = floor(excl_frac * p0 / 2) of j* (excl_frac 0.2:
+//      "20 % of the profile width"); I_av and sigma are the mean and the
+//      population standard deviation of the other filtered bins (two-pass);
+//   R17 A_w = (I_max - I_av) / sigma, score = max over widths with the R13
+//      tie-breaks; sigma = 0 or fewer than 2 off-window bins gives score 0
+//      and flag bit 0.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -403,6 +412,76 @@ void oracle_score_alg1_i64(const int64_t* x, int64_t p0, const int32_t* widths, 
     out->snr = best;
     out->width = best_w;
     out->phase = best_j;
+}
+
+// --- Section 2.2.2 Algorithm 2 ---------------------------------------------
+// Boxcar filter first (R15), then the maximum, an exclusion window of about
+// excl_frac of the profile around it (R16), and the S/N against the mean and
+// standard deviation of the rest (Eq. 5, R17).  median/mad of the record are
+// set to I_av and sigma of the winning width.
+void oracle_score_alg2_f64(const double* x, int64_t p0, const int32_t* widths, int32_t nw,
+                           double excl_frac, oracle_score* out) {
+    int64_t wmax = 0;
+    for (int32_t t = 0; t < nw; ++t) wmax = std::max<int64_t>(wmax, widths[t]);
+    std::vector<double> c((size_t)(p0 + wmax + 1));
+    c[0] = 0.0;
+    for (int64_t t = 0; t < p0 + wmax; ++t) c[t + 1] = c[t] + x[t % p0];
+    const int64_t h = (int64_t)std::floor(excl_frac * (double)p0 / 2.0);
+    const int64_t n_off = p0 - std::min<int64_t>(p0, 2 * h + 1);
+    double best = -std::numeric_limits<double>::infinity();
+    int32_t best_w = widths[0], best_j = 0;
+    double best_av = 0.0, best_sd = 0.0;
+    bool any = false;
+    std::vector<double> b((size_t)p0);
+    for (int32_t t = 0; t < nw; ++t) {
+        const int64_t w = widths[t];
+        int64_t jmax = 0;
+        for (int64_t j = 0; j < p0; ++j) {
+            b[j] = c[j + w] - c[j];
+            if (b[j] > b[jmax]) jmax = j;
+        }
+        if (n_off < 2) continue;
+        auto off = [&](int64_t j) {
+            int64_t d = j - jmax;
+            d = ((d % p0) + p0) % p0;  // cyclic distance from jmax
+            d = std::min(d, p0 - d);
+            return d > h;
+        };
+        double sum = 0.0;
+        for (int64_t j = 0; j < p0; ++j)
+            if (off(j)) sum += b[j];
+        const double av = sum / (double)n_off;
+        double ss = 0.0;
+        for (int64_t j = 0; j < p0; ++j)
+            if (off(j)) ss += (b[j] - av) * (b[j] - av);
+        const double sd = std::sqrt(ss / (double)n_off);
+        if (!(sd > 0.0)) continue;
+        const double a = (b[jmax] - av) / sd;
+        any = true;
+        if (a > best) {
+            best = a;
+            best_w = (int32_t)w;
+            best_j = (int32_t)jmax;
+            best_av = av;
+            best_sd = sd;
+        }
+    }
+    out->pad = 0;
+    if (!any) {
+        out->snr = 0.0;
+        out->width = widths[0];
+        out->phase = 0;
+        out->flags = 1;
+        out->median = 0.0;
+        out->mad = 0.0;
+        return;
+    }
+    out->snr = best;
+    out->width = best_w;
+    out->phase = best_j;
+    out->flags = 0;
+    out->median = best_av;
+    out->mad = best_sd;
 }
 
 // --- Section 2.3 search plan -------------------------------------------------

@@ -33,6 +33,10 @@ ffa_status launch_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m
 ffa_status launch_score2(const void* d_prof, int32_t precision, bool fused, int64_t count,
                          int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
                          ffa_record* d_rec, int32_t* d_status, cudaStream_t st);
+// Algorithm 2 (Section 2.2.2) with the same fused/unfused inputs.
+ffa_status launch_score_alg2(const void* d_prof, int32_t precision, bool fused, int64_t count,
+                             int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
+                             float excl_frac, ffa_record* d_rec, cudaStream_t st);
 
 constexpr int STATS_DOUBLES = 2 + 1024;  // {mean, std} + reduction partials
 

@@ -884,6 +884,255 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
     }  // trials
 }
 
+// ---------------------------------------------------------------------------
+// Algorithm 2 (Section 2.2.2, Eq. 5): boxcar first, then for each width the
+// maximum I_max (first position j*), an exclusion window of the 2h+1
+// filtered bins within cyclic distance h of j*, and
+// A_w = (I_max - I_av) / sigma over the other bins; score = max over widths.
+// Sums are taken about w * mean(x) (the mean of every filtered profile) so
+// that the FP32 sums of squares do not cancel; I_av and sigma in FP64.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T box_at(const T (&c)[R2], const Sh2& sh, const T* buf, int tid, int w, int r) {
+    using B = BoxOps<T>;
+    // cyclic box of width w starting at bin 32 tid + r, from the blocked prefix
+    const int j2 = tid * R2 + r + w;
+    const int b2 = j2 / R2, o2 = j2 % R2;
+    return B::box(B::blockdiff(sh, b2, tid), buf[sidx(b2 * R2 + o2)], c[r]);
+}
+
+template <class T, bool FUSED>
+__global__ void __launch_bounds__(T2, 1) k_score_alg2(const T* __restrict__ prof, int64_t p0_,
+                                                      int64_t m_rows, int64_t trial0, int64_t count,
+                                                      ScoreWidths wd, float excl_frac,
+                                                      ffa_record* __restrict__ rec) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Sh2& sh = *reinterpret_cast<Sh2*>(smem_raw);
+    T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(Sh2) + 15) & ~(size_t)15));
+    using B = BoxOps<T>;
+    const int p0 = (int)p0_;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int wmax = wd.w[wd.n - 1];
+    const int nbe = (p0 + wmax + R2) / R2 + 1;
+    const int h = (int)floorf(excl_frac * (float)p0 / 2.0f);
+    const int n_off = p0 - min(p0, 2 * h + 1);
+    for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+        const int64_t k = trial0 + it;
+        const T* hrow;
+        const T* trow = nullptr;
+        int sft = 0;
+        if (FUSED && m_rows > 1) {
+            hrow = prof + (k >> 1) * p0_;
+            trow = prof + ((m_rows >> 1) + (k >> 1)) * p0_;
+            sft = (int)(((k + 1) >> 1) % p0_);
+        } else if (FUSED) {
+            hrow = prof;
+        } else {
+            hrow = prof + k * p0_;
+        }
+        if (trow) {
+            const int n1 = p0 - sft;
+            for (int j = tid; j < p0; j += T2) buf[sidx(j)] = hrow[j] + (j < n1 ? trow[j + sft] : trow[j - n1]);
+        } else {
+            for (int j = tid; j < p0; j += T2) buf[sidx(j)] = hrow[j];
+        }
+        __syncthreads();
+        T x[R2];
+        const int base_pos = tid * R2;
+        int nvalid = p0 - base_pos;
+        nvalid = nvalid < 0 ? 0 : (nvalid > R2 ? R2 : nvalid);
+        float fs = 0.0f, fq = 0.0f, fm = 0.0f;
+#pragma unroll
+        for (int r = 0; r < R2; ++r) {
+            x[r] = (r < nvalid) ? buf[sidx(base_pos + r)] : (T)0;
+            if (r < nvalid) fs += (float)x[r];
+        }
+        blk_stats(fs, fq, fm, sh);
+        const float mean = fs / (float)p0;
+        // blocked cyclic prefix (as in k_score2)
+        const bool one_wrap = nbe * R2 <= 2 * p0;
+        const int eb2 = tid + T2;
+        T tot = 0, tot2 = 0;
+        if (eb2 < nbe) {
+            for (int r = 0; r < R2; ++r) {
+                const int j = eb2 * R2 + r;
+                const T v = buf[sidx(one_wrap ? j - p0 : j % p0)];
+                buf[sidx(j)] = tot2;
+                tot2 = tot2 + v;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R2; ++r) {
+            const int j = base_pos + r;
+            T v = x[r];
+            if (j >= p0) v = (tid < nbe) ? buf[sidx(one_wrap ? j - p0 : j % p0)] : (T)0;
+            x[r] = tot;
+            tot = tot + v;
+        }
+        __syncthreads();
+        {
+            T* blk = buf + sidx(base_pos);
+#pragma unroll
+            for (int r = 0; r < R2; r += 4) *reinterpret_cast<int4*>(blk + r) = *reinterpret_cast<const int4*>(&x[r]);
+        }
+        if constexpr (Traits<T>::is_int) {
+            uint32_t t0, t1;
+            const uint32_t ex0 = blk_exscan_u((uint32_t)tot, sh, &t0);
+            int* cbi = reinterpret_cast<int*>(sh.cbh);
+            cbi[tid] = (int)ex0;
+            if (nbe > T2) {
+                const uint32_t ex1 = blk_exscan_u(eb2 < nbe ? (uint32_t)tot2 : 0u, sh, &t1);
+                if (eb2 <= MAXB) cbi[eb2] = (int)(t0 + ex1);
+            } else if (tid == 0) {
+                cbi[T2] = (int)t0;
+            }
+        } else {
+            float oh, ol, th, tl, oh2, ol2, th2, tl2;
+            blk_exscan_ff((float)tot, sh, oh, ol, th, tl);
+            sh.cbh[tid] = oh;
+            sh.cbl[tid] = ol;
+            if (nbe > T2) {
+                blk_exscan_ff(eb2 < nbe ? (float)tot2 : 0.0f, sh, oh2, ol2, th2, tl2);
+                if (eb2 <= MAXB) {
+                    float hh, ll;
+                    ff_add(th, tl, oh2, ol2, hh, ll);
+                    sh.cbh[eb2] = hh;
+                    sh.cbl[eb2] = ll;
+                }
+            } else if (tid == 0) {
+                sh.cbh[T2] = th;
+                sh.cbl[T2] = tl;
+            }
+        }
+        __syncthreads();
+        double best = -INFINITY, best_av = 0.0;
+        int best_w = 0, best_j = 0;
+        for (int wi = 0; wi < wd.n; ++wi) {
+            const int w = wd.w[wi];
+            const float ref = (float)w * mean;  // mean of the filtered profile
+            T m = B::lowest();
+            int mpos = 0x7fffffff;
+            float s1 = 0.0f, s2 = 0.0f;
+            if (nvalid > 0) {
+#pragma unroll
+                for (int r = 0; r < R2; ++r) {
+                    if (r < nvalid) {
+                        const T bx = box_at(x, sh, buf, tid, w, r);
+                        if (bx > m) {
+                            m = bx;
+                            mpos = base_pos + r;
+                        }
+                        const float d = (float)bx - ref;
+                        s1 += d;
+                        s2 = fmaf(d, d, s2);
+                    }
+                }
+            }
+            // block: max with first position, and the two sums
+            float mf = (float)m;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float om = __shfl_xor_sync(0xffffffffu, mf, o);
+                const int op = __shfl_xor_sync(0xffffffffu, mpos, o);
+                if (om > mf || (om == mf && op < mpos)) {
+                    mf = om;
+                    mpos = op;
+                }
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            }
+            __syncthreads();
+            if (lane == 0) {
+                sh.wred[0][warp] = mf;
+                sh.wredi[0][warp] = mpos;
+                sh.wred[1][warp] = s1;
+                sh.wred[2][warp] = s2;
+            }
+            __syncthreads();
+            mf = sh.wred[0][lane];
+            mpos = sh.wredi[0][lane];
+            s1 = sh.wred[1][lane];
+            s2 = sh.wred[2][lane];
+            for (int o = 16; o > 0; o >>= 1) {
+                const float om = __shfl_xor_sync(0xffffffffu, mf, o);
+                const int op = __shfl_xor_sync(0xffffffffu, mpos, o);
+                if (om > mf || (om == mf && op < mpos)) {
+                    mf = om;
+                    mpos = op;
+                }
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            }
+            const int jstar = mpos;
+            // sums over the exclusion window around j*
+            float w1 = 0.0f, w2 = 0.0f;
+            if (nvalid > 0) {
+#pragma unroll
+                for (int r = 0; r < R2; ++r) {
+                    const int j = base_pos + r;
+                    int d = j - jstar;
+                    if (d < 0) d = -d;
+                    d = min(d, p0 - d);
+                    if (r < nvalid && d <= h) {
+                        const T bx = box_at(x, sh, buf, tid, w, r);
+                        const float dd = (float)bx - ref;
+                        w1 += dd;
+                        w2 = fmaf(dd, dd, w2);
+                    }
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                w1 += __shfl_xor_sync(0xffffffffu, w1, o);
+                w2 += __shfl_xor_sync(0xffffffffu, w2, o);
+            }
+            __syncthreads();
+            if (lane == 0) {
+                sh.wred[3][warp] = w1;
+                sh.wred[4][warp] = w2;
+            }
+            __syncthreads();
+            w1 = sh.wred[3][lane];
+            w2 = sh.wred[4][lane];
+            for (int o = 16; o > 0; o >>= 1) {
+                w1 += __shfl_xor_sync(0xffffffffu, w1, o);
+                w2 += __shfl_xor_sync(0xffffffffu, w2, o);
+            }
+            if (n_off >= 2) {
+                const double a1 = ((double)s1 - (double)w1) / n_off;        // mean offset from ref
+                const double var = ((double)s2 - (double)w2) / n_off - a1 * a1;
+                const double sd = var > 0.0 ? sqrt(var) : 0.0;
+                const double av = (double)ref + a1;
+                if (sd > 0.0) {
+                    const double a = ((double)mf - av) / sd;
+                    if (a > best) {
+                        best = a;
+                        best_w = wi;
+                        best_j = jstar;
+                        best_av = av;
+                    }
+                }
+            }
+        }
+        (void)best_av;
+        if (tid == 0) {
+            ffa_record out;
+            if (best == -INFINITY) {
+                out.snr = 0.0f;
+                out.width = wd.w[0];
+                out.phase = 0;
+                out.flags = 1;
+            } else {
+                out.snr = (float)best;
+                out.width = wd.w[best_w];
+                out.phase = best_j;
+                out.flags = 0;
+            }
+            rec[it] = out;
+        }
+        __syncthreads();
+    }
+}
+
 size_t score2_smem_bytes(int64_t p0, int wmax, size_t elem) {
     int64_t nbe = (p0 + wmax + R2) / R2 + 1;
     int64_t nbins = (nbe > T2 ? nbe : T2) * R2 + R2;
@@ -916,6 +1165,36 @@ ffa_status launch_score2(const void* d_prof, int32_t precision, bool fused, int6
     }
 #undef FFA_S2
     FFA_LAUNCH_CHECK("k_score2");
+    count_launch();
+    return FFA_OK;
+}
+
+ffa_status launch_score_alg2(const void* d_prof, int32_t precision, bool fused, int64_t count,
+                             int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
+                             float excl_frac, ffa_record* d_rec, cudaStream_t st) {
+    if (count <= 0) return FFA_OK;
+    const int wmax = wd.w[wd.n - 1];
+    if (p0 < 1 || (p0 + wmax + R2) / R2 + 1 > MAXB || (p0 + R2 - 1) / R2 > T2)
+        return fail(FFA_ERR_UNSUPPORTED, "score: profile longer than 32768 bins");
+    const size_t smem = score2_smem_bytes(p0, wmax, 4);
+    if (smem > 227 * 1024) return fail(FFA_ERR_UNSUPPORTED, "score: profile too long for shared memory");
+    int dev = 0, nsm = 0;
+    FFA_CUDA_TRY(cudaGetDevice(&dev));
+    FFA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)(count < nsm ? count : nsm);
+    ffa_status es;
+#define FFA_A2(TT, FF)                                                                          \
+    es = ensure_smem((const void*)k_score_alg2<TT, FF>, smem);                                  \
+    if (es != FFA_OK) return es;                                                                \
+    k_score_alg2<TT, FF><<<grid, T2, smem, st>>>((const TT*)d_prof, p0, m_rows, trial0, count, wd, \
+                                                 excl_frac, d_rec);
+    if (precision == FFA_FOLD_F32) {
+        if (fused) { FFA_A2(float, true) } else { FFA_A2(float, false) }
+    } else {
+        if (fused) { FFA_A2(int32_t, true) } else { FFA_A2(int32_t, false) }
+    }
+#undef FFA_A2
+    FFA_LAUNCH_CHECK("k_score_alg2");
     count_launch();
     return FFA_OK;
 }

@@ -245,15 +245,16 @@ struct TimingRec {
 std::mutex g_tmu;
 bool g_timing = false;
 std::vector<TimingRec> g_trec;
+constexpr int64_t TIMING_SAMPLE = 64;  // per-kernel timing: every 64th base period of an octave
 
 struct PhaseTimer {
     bool on = false;
     TimingRec r;
     cudaStream_t st;
-    PhaseTimer(int phase, int octave, cudaStream_t s) : st(s) {
+    PhaseTimer(int phase, int octave, cudaStream_t s, bool enabled = true) : st(s) {
         {
             std::lock_guard<std::mutex> lk(g_tmu);
-            on = g_timing;
+            on = g_timing && enabled;
         }
         if (!on) return;
         r.phase = phase;
@@ -306,6 +307,10 @@ ffa_status ffa_plan_create(const ffa_search_config* cfg, int64_t n, ffa_plan** o
         return fail(FFA_ERR_ARG, "plan: in_type must be FFA_IN_F32 or FFA_IN_U8");
     if (cfg->precision != FFA_FOLD_F32 && cfg->precision != FFA_FOLD_I8)
         return fail(FFA_ERR_ARG, "plan: bad precision");
+    if (cfg->scorer != FFA_SCORE_ALG1 && cfg->scorer != FFA_SCORE_ALG2)
+        return fail(FFA_ERR_ARG, "plan: bad scorer");
+    if (!(cfg->alg2_window >= 0.0f && cfg->alg2_window < 1.0f))
+        return fail(FFA_ERR_ARG, "plan: alg2_window must be in [0, 1)");
     if (cfg->n_widths_fixed < 0 || cfg->n_widths_fixed > 16)
         return fail(FFA_ERR_ARG, "plan: n_widths_fixed must be in [0, 16]");
     if (cfg->n_widths_fixed == 0 && !(cfg->duty_max > 0.0))
@@ -438,14 +443,19 @@ ffa_status ffa_plan_entries(const ffa_plan* p, ffa_plan_entry* out, int64_t cap)
     return FFA_OK;
 }
 
-ffa_status ffa_search(const ffa_plan* p, const void* d_series, void* d_ws, size_t ws_bytes,
-                      ffa_record* d_records, int32_t* d_status, void* stream) {
+// The pipeline for plan entries [e0, e1): every octave holding one of them is
+// prepared (downsampled, dereddened, normalised); only those base periods are
+// folded and scored.
+static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_ws, size_t ws_bytes,
+                               ffa_record* d_records, int32_t* d_status, cudaStream_t st, int64_t e0,
+                               int64_t e1) {
     if (!p) return fail(FFA_ERR_ARG, "search: null plan");
-    if (p->n_trials == 0) return FFA_OK;
+    const int64_t ne = (int64_t)p->entries.size();
+    if (e0 < 0 || e1 > ne || e0 > e1) return fail(FFA_ERR_ARG, "search: entry range out of bounds");
+    if (e0 == e1 || p->n_trials == 0) return FFA_OK;
     if (!d_series || !d_ws || !d_records) return fail(FFA_ERR_ARG, "search: null buffer");
     if (ws_bytes < p->ws_bytes) return fail(FFA_ERR_OOM, "search: workspace too small");
     if ((uintptr_t)d_ws % 256 != 0) return fail(FFA_ERR_ARG, "search: workspace not 256-byte aligned");
-    cudaStream_t st = as_stream(stream);
     char* ws = (char*)d_ws;
     double* raw[2] = {(double*)(ws + p->off_raw_a), (double*)(ws + p->off_raw_b)};
     double* resid = (double*)(ws + p->off_resid);
@@ -454,17 +464,20 @@ ffa_status ffa_search(const ffa_plan* p, const void* d_series, void* d_ws, size_
     void* plane0 = ws + p->off_plane0;
     void* plane1 = ws + p->off_plane1;
     const ffa_search_config& c = p->cfg;
+    const int32_t last_oct = p->entries[(size_t)(e1 - 1)].octave;
+    const int32_t first_oct = p->entries[(size_t)e0].octave;
     ffa_status s = launch_downsample(d_series, c.in_type, p->n, c.downsample0, raw[0], st);
     if (s != FFA_OK) return s;
     int64_t n_o = p->n0;
-    for (int32_t o = 0; o < p->n_octaves; ++o) {
-        PhaseTimer prep_t(0, o, st);
+    for (int32_t o = 0; o <= last_oct; ++o) {
         double* cur = raw[o & 1];
         if (o > 0) {
             s = launch_downsample(raw[(o - 1) & 1], FFA_IN_F64, n_o, 2, cur, st);
             if (s != FFA_OK) return s;
             n_o /= 2;
         }
+        if (o < first_oct) continue;  // only the downsampling chain is needed
+        PhaseTimer prep_t(0, o, st);
         if (p->window > 1) {
             s = launch_detrend(cur, n_o, p->window, resid, d_status, st);
         } else {
@@ -477,22 +490,65 @@ ffa_status ffa_search(const ffa_plan* p, const void* d_series, void* d_ws, size_
         if (s != FFA_OK) return s;
         prep_t.stop();
         PhaseTimer fold_t(1, o, st);
-        for (int64_t t = 0; t < p->oct_count[o]; ++t) {
-            const ffa_plan_entry& e = p->entries[(size_t)(p->oct_first[o] + t)];
+        const int64_t a = std::max<int64_t>(e0, p->oct_first[o]);
+        const int64_t b = std::min<int64_t>(e1, p->oct_first[o] + p->oct_count[o]);
+        for (int64_t t = a; t < b; ++t) {
+            const ffa_plan_entry& e = p->entries[(size_t)t];
             int m = 0;
             while ((1 << m) < e.m_rows) ++m;
+            // per-kernel timing of every TIMING_SAMPLE-th base period of an octave
+            const bool sample = ((t - p->oct_first[o]) % TIMING_SAMPLE) == 0;
             // all but the last stage; the scorer applies the last one while loading
+            PhaseTimer fold_k(2, o, st, sample);
             s = launch_fold(z, c.precision, e.p0, e.m_data, e.m_rows, m > 0 ? m - 1 : 0, plane0,
                             plane1, st);
             if (s != FFA_OK) return s;
+            fold_k.stop();
             ScoreWidths wd;
             wd.n = e.n_widths;
             for (int k = 0; k < 16; ++k) wd.w[k] = e.widths[k];
-            s = launch_score2(plane0, c.precision, true, e.m_rows, 0, e.p0, e.m_rows, wd,
-                              d_records + e.first_trial, d_status, st);
+            PhaseTimer score_k(3, o, st, sample);
+            if (c.scorer == FFA_SCORE_ALG2)
+                s = launch_score_alg2(plane0, c.precision, true, e.m_rows, 0, e.p0, e.m_rows, wd,
+                                      c.alg2_window > 0.0f ? c.alg2_window : 0.2f,
+                                      d_records + e.first_trial, st);
+            else
+                s = launch_score2(plane0, c.precision, true, e.m_rows, 0, e.p0, e.m_rows, wd,
+                                  d_records + e.first_trial, d_status, st);
             if (s != FFA_OK) return s;
+            score_k.stop();
         }
         fold_t.stop();
+    }
+    return FFA_OK;
+}
+
+ffa_status ffa_search(const ffa_plan* p, const void* d_series, void* d_ws, size_t ws_bytes,
+                      ffa_record* d_records, int32_t* d_status, void* stream) {
+    if (!p) return fail(FFA_ERR_ARG, "search: null plan");
+    return search_range(p, d_series, d_ws, ws_bytes, d_records, d_status, as_stream(stream), 0,
+                        (int64_t)p->entries.size());
+}
+
+ffa_status ffa_search_entries(const ffa_plan* p, const void* d_series, int64_t entry_begin,
+                              int64_t entry_end, void* d_ws, size_t ws_bytes, ffa_record* d_records,
+                              int32_t* d_status, void* stream) {
+    return search_range(p, d_series, d_ws, ws_bytes, d_records, d_status, as_stream(stream),
+                        entry_begin, entry_end);
+}
+
+ffa_status ffa_search_batch(const ffa_plan* const* plans, const void* const* d_series, int32_t count,
+                            void* d_ws, size_t ws_bytes, ffa_record* const* d_records,
+                            int32_t* d_status, void* stream) {
+    if (count < 0 || (count > 0 && (!plans || !d_series || !d_records)))
+        return fail(FFA_ERR_ARG, "search_batch: null argument");
+    for (int32_t i = 0; i < count; ++i) {
+        if (!plans[i]) return fail(FFA_ERR_ARG, "search_batch: null plan");
+        if (ws_bytes < plans[i]->ws_bytes) return fail(FFA_ERR_OOM, "search_batch: workspace too small");
+    }
+    for (int32_t i = 0; i < count; ++i) {
+        ffa_status s = ffa_search(plans[i], d_series[i], d_ws, ws_bytes, d_records[i], d_status, stream);
+        if (s != FFA_OK) return s;
     }
     return FFA_OK;
 }
@@ -506,7 +562,7 @@ ffa_status ffa_timing_enable(int32_t on) {
 }
 
 ffa_status ffa_timing_read(double* ms, int32_t* counts, int32_t cap) {
-    if (!ms || !counts || cap < 128) return fail(FFA_ERR_ARG, "timing_read: need cap >= 128");
+    if (!ms || !counts || cap < 256) return fail(FFA_ERR_ARG, "timing_read: need cap >= 256");
     std::vector<TimingRec> recs;
     {
         std::lock_guard<std::mutex> lk(g_tmu);
@@ -553,16 +609,20 @@ ffa_status ffa_wait(void* stream, const int32_t* d_status, int32_t timeout_ms) {
     return FFA_OK;
 }
 
-ffa_status ffa_candidates(const ffa_plan* p, const ffa_record* d_records, double snr_min,
-                          int32_t top_k, void* d_ws, size_t ws_bytes, ffa_candidate* out,
-                          int32_t* n_out, int64_t* best, int32_t* d_status, void* stream,
-                          int32_t timeout_ms) {
+// Candidates among the trials of plan entries [e0, e1) (records outside are
+// not read).
+static ffa_status candidates_range(const ffa_plan* p, int64_t e0, int64_t e1, const ffa_record* d_records,
+                                   double snr_min, int32_t top_k, void* d_ws, size_t ws_bytes,
+                                   ffa_candidate* out, int32_t* n_out, int64_t* best, int32_t* d_status,
+                                   void* stream, int32_t timeout_ms) {
     if (!p || !n_out || !best) return fail(FFA_ERR_ARG, "candidates: null argument");
     if (top_k < 0 || top_k > CAND_MAX) return fail(FFA_ERR_ARG, "candidates: top_k must be in [0, 4096]");
     if (top_k > 0 && !out) return fail(FFA_ERR_ARG, "candidates: null output");
+    const int64_t ne = (int64_t)p->entries.size();
+    if (e0 < 0 || e1 > ne || e0 > e1) return fail(FFA_ERR_ARG, "candidates: entry range out of bounds");
     *n_out = 0;
     *best = -1;
-    if (p->n_trials == 0) return FFA_OK;
+    if (e0 == e1 || p->n_trials == 0) return FFA_OK;
     if (!d_records || !d_ws) return fail(FFA_ERR_ARG, "candidates: null buffer");
     if (ws_bytes < p->ws_bytes) return fail(FFA_ERR_OOM, "candidates: workspace too small");
     cudaStream_t st = as_stream(stream);
@@ -570,17 +630,20 @@ ffa_status ffa_candidates(const ffa_plan* p, const ffa_record* d_records, double
     CandCtl* ctl = (CandCtl*)base;
     unsigned long long* keys = (unsigned long long*)(base + align256(sizeof(CandCtl)));
     CandOut* cout = (CandOut*)(base + align256(sizeof(CandCtl)) + sizeof(unsigned long long) * CAND_MAX);
-    const int64_t n = p->n_trials;
+    const int64_t t0 = p->entries[(size_t)e0].first_trial;
+    const ffa_plan_entry& el = p->entries[(size_t)(e1 - 1)];
+    const int64_t n = el.first_trial + el.m_rows - t0;
+    const ffa_record* rec = d_records + t0;
     const float smin = (float)snr_min;
     const int grid = 152 * 8;
     k_cand_init<<<1, 256, 0, st>>>(ctl);
-    k_cand_count<<<grid, 256, 0, st>>>(d_records, n, smin, ctl);
+    k_cand_count<<<grid, 256, 0, st>>>(rec, n, smin, ctl);
     for (int pass = 0; pass < 8; ++pass) {
-        k_cand_hist<<<grid, 256, 0, st>>>(d_records, n, smin, pass, ctl);
+        k_cand_hist<<<grid, 256, 0, st>>>(rec, n, smin, pass, ctl);
         k_cand_pick<<<1, 32, 0, st>>>(pass, top_k, ctl);
     }
-    k_cand_compact<<<grid, 256, 0, st>>>(d_records, n, smin, ctl, keys);
-    k_cand_sort<<<1, 1024, 0, st>>>(d_records, ctl, keys, cout);
+    k_cand_compact<<<grid, 256, 0, st>>>(rec, n, smin, ctl, keys);
+    k_cand_sort<<<1, 1024, 0, st>>>(rec, ctl, keys, cout);
     FFA_LAUNCH_CHECK("candidates kernels");
     count_launch(21);
     ffa_status s = ffa_wait(stream, d_status, timeout_ms);
@@ -590,27 +653,45 @@ ffa_status ffa_candidates(const ffa_plan* p, const ffa_record* d_records, double
     uint32_t m = std::min<uint32_t>(h.n_out, (uint32_t)top_k);
     std::vector<CandOut> buf(m);
     if (m > 0) FFA_CUDA_TRY(cudaMemcpy(buf.data(), cout, sizeof(CandOut) * m, cudaMemcpyDeviceToHost));
-    if (h.best_key != ~0ull) *best = (int64_t)(uint32_t)(h.best_key & 0xffffffffull);
+    if (h.best_key != ~0ull) *best = t0 + (int64_t)(uint32_t)(h.best_key & 0xffffffffull);
     const ffa_search_config& c = p->cfg;
     for (uint32_t t = 0; t < m; ++t) {
         const CandOut& o = buf[t];
+        const int64_t trial = t0 + o.trial;
         // entry holding this trial: the last one with first_trial <= trial
-        auto it = std::upper_bound(p->entries.begin(), p->entries.end(), o.trial,
+        auto it = std::upper_bound(p->entries.begin(), p->entries.end(), trial,
                                    [](int64_t v, const ffa_plan_entry& e) { return v < e.first_trial; });
         const ffa_plan_entry& e = *(it - 1);
         ffa_candidate& d = out[t];
-        d.trial = o.trial;
+        d.trial = trial;
         d.octave = e.octave;
         d.p0 = e.p0;
-        d.k = (int32_t)(o.trial - e.first_trial);
+        d.k = (int32_t)(trial - e.first_trial);
         d.snr = o.snr;
         d.width = o.width;
         d.phase = o.phase;
-        double scale = c.tsamp_s * (double)c.downsample0 * std::ldexp(1.0, e.octave);
+        const double scale = c.tsamp_s * (double)c.downsample0 * std::ldexp(1.0, e.octave);
         d.period_s = ((double)e.p0 + (double)d.k / (double)(e.m_rows - 1)) * scale;
     }
     *n_out = (int32_t)m;
     return FFA_OK;
+}
+
+ffa_status ffa_candidates(const ffa_plan* p, const ffa_record* d_records, double snr_min,
+                          int32_t top_k, void* d_ws, size_t ws_bytes, ffa_candidate* out,
+                          int32_t* n_out, int64_t* best, int32_t* d_status, void* stream,
+                          int32_t timeout_ms) {
+    if (!p) return fail(FFA_ERR_ARG, "candidates: null plan");
+    return candidates_range(p, 0, (int64_t)p->entries.size(), d_records, snr_min, top_k, d_ws, ws_bytes,
+                            out, n_out, best, d_status, stream, timeout_ms);
+}
+
+ffa_status ffa_candidates_entries(const ffa_plan* p, int64_t entry_begin, int64_t entry_end,
+                                  const ffa_record* d_records, double snr_min, int32_t top_k,
+                                  void* d_ws, size_t ws_bytes, ffa_candidate* out, int32_t* n_out,
+                                  int64_t* best, int32_t* d_status, void* stream, int32_t timeout_ms) {
+    return candidates_range(p, entry_begin, entry_end, d_records, snr_min, top_k, d_ws, ws_bytes, out,
+                            n_out, best, d_status, stream, timeout_ms);
 }
 
 // ---- step entry points ------------------------------------------------------
@@ -664,6 +745,26 @@ ffa_status ffa_score(const void* d_profiles, int32_t precision, int64_t count, i
     if (precision != FFA_FOLD_F32 && precision != FFA_FOLD_I8) return fail(FFA_ERR_ARG, "score: bad precision");
     return launch_score2(d_profiles, precision, false, count, 0, p0, 1, wd, d_records, d_status,
                          as_stream(stream));
+}
+
+ffa_status ffa_score_alg2(const void* d_profiles, int32_t precision, int64_t count, int64_t p0,
+                          const int32_t* widths, int32_t n_widths, float excl_frac,
+                          ffa_record* d_records, void* stream) {
+    if (count < 0 || p0 < 1) return fail(FFA_ERR_ARG, "score_alg2: need count >= 0 and p0 >= 1");
+    if (n_widths < 1 || n_widths > 16 || !widths) return fail(FFA_ERR_ARG, "score_alg2: 1..16 widths");
+    if (!(excl_frac >= 0.0f && excl_frac < 1.0f)) return fail(FFA_ERR_ARG, "score_alg2: excl_frac in [0, 1)");
+    ScoreWidths wd;
+    wd.n = n_widths;
+    for (int t = 0; t < 16; ++t) wd.w[t] = t < n_widths ? widths[t] : 0;
+    for (int t = 0; t < n_widths; ++t) {
+        int32_t w = widths[t];
+        if (w < 1 || (w & (w - 1)) != 0 || (t > 0 && w <= widths[t - 1]))
+            return fail(FFA_ERR_UNSUPPORTED, "score_alg2: widths must be increasing powers of two");
+    }
+    if (count > 0 && (!d_profiles || !d_records)) return fail(FFA_ERR_ARG, "score_alg2: null buffer");
+    if (precision != FFA_FOLD_F32 && precision != FFA_FOLD_I8) return fail(FFA_ERR_ARG, "score_alg2: bad precision");
+    return launch_score_alg2(d_profiles, precision, false, count, 0, p0, 1, wd, excl_frac, d_records,
+                             as_stream(stream));
 }
 
 }  // extern "C"

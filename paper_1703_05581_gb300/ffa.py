@@ -23,6 +23,7 @@ _lib = C.CDLL(LIB_PATH)
 
 OK, ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_CANCELLED, ERR_UNSUPPORTED, ERR_DEVICE = range(8)
 IN_F32, IN_U8, IN_F64 = 0, 1, 2
+SCORE_ALG1, SCORE_ALG2 = 0, 1
 FOLD_F32, FOLD_I8 = 0, 1
 STATS_DOUBLES = 1026
 NOALLOC_FOLD_MAX_ELEMS = 8 * 1024 * 1024
@@ -39,7 +40,8 @@ class SearchConfig(C.Structure):
                 ("period_max_s", C.c_double), ("duty_max", C.c_double),
                 ("downsample0", C.c_int32), ("detrend_window", C.c_int32),
                 ("min_rows", C.c_int32), ("in_type", C.c_int32), ("precision", C.c_int32),
-                ("n_widths_fixed", C.c_int32), ("widths_fixed", C.c_int32 * 16)]
+                ("n_widths_fixed", C.c_int32), ("widths_fixed", C.c_int32 * 16),
+                ("scorer", C.c_int32), ("alg2_window", C.c_float)]
 
 
 class Record(C.Structure):
@@ -77,8 +79,12 @@ _sig = {
     "ffa_plan_info": ([_P, _P, _P, _P, _P, _P], C.c_int),
     "ffa_plan_entries": ([_P, _P, _i64], C.c_int),
     "ffa_search": ([_P, _P, _P, C.c_size_t, _P, _P, _P], C.c_int),
+    "ffa_search_entries": ([_P, _P, _i64, _i64, _P, C.c_size_t, _P, _P, _P], C.c_int),
+    "ffa_search_batch": ([_P, _P, _i32, _P, C.c_size_t, _P, _P, _P], C.c_int),
     "ffa_candidates": ([_P, _P, C.c_double, _i32, _P, C.c_size_t, _P, _P, _P, _P, _P, _i32],
                        C.c_int),
+    "ffa_candidates_entries": ([_P, _i64, _i64, _P, C.c_double, _i32, _P, C.c_size_t, _P, _P, _P, _P,
+                                _P, _i32], C.c_int),
     "ffa_wait": ([_P, _P, _i32], C.c_int),
     "ffa_downsample": ([_P, _i32, _i64, _i64, _P, _P], C.c_int),
     "ffa_detrend": ([_P, _i64, _i32, _P, _P, _P], C.c_int),
@@ -86,6 +92,7 @@ _sig = {
     "ffa_fold": ([_P, _i32, _i64, _i64, _i64, _P, _P, _P], C.c_int),
     "ffa_fold_noalloc": ([_P, _i32, _i64, _i64, _i64, _P, _P], C.c_int),
     "ffa_score": ([_P, _i32, _i64, _i64, _P, _i32, _P, _P, _P], C.c_int),
+    "ffa_score_alg2": ([_P, _i32, _i64, _i64, _P, _i32, C.c_float, _P, _P], C.c_int),
     "ffa_timing_enable": ([_i32], C.c_int),
     "ffa_launch_count": ([], C.c_int64),
     "ffa_timing_read": ([_P, _P, _i32], C.c_int),
@@ -129,6 +136,8 @@ class Config:
     in_type: int = IN_F32
     precision: int = FOLD_F32
     widths: tuple = field(default_factory=tuple)
+    scorer: int = SCORE_ALG1
+    alg2_window: float = 0.0
 
     def c(self) -> SearchConfig:
         c = SearchConfig()
@@ -140,6 +149,7 @@ class Config:
         c.n_widths_fixed = len(self.widths)
         for i, w in enumerate(self.widths):
             c.widths_fixed[i] = int(w)
+        c.scorer, c.alg2_window = self.scorer, self.alg2_window
         return c
 
 
@@ -205,6 +215,38 @@ def search(plan: Plan, series: torch.Tensor, workspace: torch.Tensor | None = No
     return records
 
 
+def search_entries(plan: Plan, series: torch.Tensor, entry_begin: int, entry_end: int,
+                   workspace: torch.Tensor | None = None, records: torch.Tensor | None = None,
+                   status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Search only plan entries [entry_begin, entry_end); records of other trials untouched."""
+    assert series.is_cuda and series.is_contiguous() and series.numel() == plan.n
+    workspace = plan.workspace(series.device) if workspace is None else workspace
+    records = plan.records(series.device) if records is None else records
+    status = status_word(series.device) if status is None else status
+    _check(_lib.ffa_search_entries(plan._h, _ptr(series), int(entry_begin), int(entry_end),
+                                   _ptr(workspace), workspace.numel(), _ptr(records), _ptr(status),
+                                   _stream(stream)))
+    return records
+
+
+def search_batch(plans, series, workspace: torch.Tensor | None = None, records=None,
+                 status: torch.Tensor | None = None, stream=None):
+    """Search a batch of series (uneven lengths), each with its own plan; returns the record tensors."""
+    assert len(plans) == len(series)
+    dev = series[0].device
+    need = max(p.workspace_bytes for p in plans)
+    workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev) if workspace is None else workspace
+    records = [p.records(dev) for p in plans] if records is None else records
+    status = status_word(dev) if status is None else status
+    n = len(plans)
+    hp = (C.c_void_p * n)(*[p._h.value for p in plans])
+    hs = (C.c_void_p * n)(*[t.data_ptr() for t in series])
+    hr = (C.c_void_p * n)(*[r.data_ptr() for r in records])
+    _check(_lib.ffa_search_batch(hp, hs, n, _ptr(workspace), workspace.numel(), hr, _ptr(status),
+                                 _stream(stream)))
+    return records
+
+
 def records_numpy(records: torch.Tensor, n: int) -> np.ndarray:
     return records[:n].cpu().numpy().view(RECORD_DTYPE).reshape(-1)
 
@@ -223,6 +265,20 @@ def candidates(plan: Plan, records: torch.Tensor, workspace: torch.Tensor, snr_m
     return out[: n_out.value], best.value
 
 
+def candidates_entries(plan: Plan, entry_begin: int, entry_end: int, records: torch.Tensor,
+                       workspace: torch.Tensor, snr_min: float, top_k: int = 64,
+                       status: torch.Tensor | None = None, stream=None, timeout_ms: int = 600000):
+    """Candidates among the trials of plan entries [entry_begin, entry_end)."""
+    status = status_word(records.device) if status is None else status
+    out = np.zeros(max(top_k, 1), CANDIDATE_DTYPE)
+    n_out, best = C.c_int32(), C.c_int64()
+    _check(_lib.ffa_candidates_entries(plan._h, int(entry_begin), int(entry_end), _ptr(records),
+                                       float(snr_min), int(top_k), _ptr(workspace), workspace.numel(),
+                                       out.ctypes.data_as(C.c_void_p), C.byref(n_out), C.byref(best),
+                                       _ptr(status), _stream(stream), int(timeout_ms)))
+    return out[: n_out.value], best.value
+
+
 def wait(status: torch.Tensor | None = None, stream=None, timeout_ms: int = 600000) -> None:
     _check(_lib.ffa_wait(_stream(stream), _ptr(status), int(timeout_ms)))
 
@@ -235,12 +291,18 @@ def launch_count() -> int:
     return int(_lib.ffa_launch_count())
 
 
+TIMING_SAMPLE = 64  # phases 2/3 time every 64th base period of each octave
+
+
 def timing_read():
-    """Return (ms[2, 64], counts[2, 64]) summed per (phase, octave); clears the record."""
-    ms = np.zeros(128, np.float64)
-    cnt = np.zeros(128, np.int32)
-    _check(_lib.ffa_timing_read(ms.ctypes.data_as(C.c_void_p), cnt.ctypes.data_as(C.c_void_p), 128))
-    return ms.reshape(2, 64), cnt.reshape(2, 64)
+    """Return (ms[4, 64], counts[4, 64]) summed per (phase, octave); clears the record.
+
+    Phases: 0 preparation, 1 fold + score, 2 fold launches and 3 scoring launch
+    of every TIMING_SAMPLE-th base period of the octave."""
+    ms = np.zeros(256, np.float64)
+    cnt = np.zeros(256, np.int32)
+    _check(_lib.ffa_timing_read(ms.ctypes.data_as(C.c_void_p), cnt.ctypes.data_as(C.c_void_p), 256))
+    return ms.reshape(4, 64), cnt.reshape(4, 64)
 
 
 # ---- individual steps --------------------------------------------------------
@@ -292,4 +354,15 @@ def score(profiles: torch.Tensor, widths, status: torch.Tensor | None = None,
     rec = torch.empty((max(count, 1), 4), dtype=torch.int32, device=profiles.device)
     _check(_lib.ffa_score(_ptr(profiles), prec, count, p0, w.ctypes.data_as(C.c_void_p), w.size,
                           _ptr(rec), _ptr(status), _stream(stream)))
+    return rec
+
+
+def score_alg2(profiles: torch.Tensor, widths, excl_frac: float = 0.2, stream=None) -> torch.Tensor:
+    """Algorithm 2 (Section 2.2.2) on (count, p0) profiles; returns (count, 4) int32 records."""
+    prec = FOLD_F32 if profiles.dtype == torch.float32 else FOLD_I8
+    count, p0 = profiles.shape
+    w = np.ascontiguousarray(widths, np.int32)
+    rec = torch.empty((max(count, 1), 4), dtype=torch.int32, device=profiles.device)
+    _check(_lib.ffa_score_alg2(_ptr(profiles), prec, count, p0, w.ctypes.data_as(C.c_void_p), w.size,
+                               float(excl_frac), _ptr(rec), _stream(stream)))
     return rec

@@ -176,6 +176,43 @@ def test_edge_cases(F, orc, dev):
     assert ei.value.status == F.ERR_OOM
 
 
+def test_entry_ranges_and_batch(F, orc, dev):
+    """Two ranges of base periods give the full search's records and candidates;
+    a batch of uneven series gives each series' own search."""
+    import torch
+    from paper_1703_05581_gb300 import shard, synth
+    x = synth.plain_series(seed=9)
+    kw = plain_kw()
+    plan = F.Plan(F.Config(**kw), x.size)
+    xs = torch.from_numpy(x).to(dev)
+    ws = plan.workspace(dev)
+    full = F.search(plan, xs, workspace=ws)
+    cf, bf = F.candidates(plan, full, ws, snr_min=6.0, top_k=20)
+    full_np = F.records_numpy(full, plan.n_trials)
+    parts = shard.split_entries(plan.entries, 3)
+    rec = plan.records(dev)
+    lists, bests = [], []
+    for b, e in parts:
+        F.search_entries(plan, xs, b, e, workspace=ws, records=rec)
+        c, bb = F.candidates_entries(plan, b, e, rec, ws, snr_min=6.0, top_k=20)
+        lists.append(c)
+        bests.append(bb)
+    got = F.records_numpy(rec, plan.n_trials)
+    assert np.array_equal(got.view(np.uint8), full_np.view(np.uint8))
+    merged = shard.merge_candidates(lists, 20)
+    assert np.array_equal(merged["trial"], cf["trial"])
+    assert bf in bests
+    # batch of uneven series
+    series = [synth.make_series(synth.SeriesSpec(n=n, seed=40 + i)) for i, n in
+              enumerate([30000, 65536, 47000])]
+    plans = [F.Plan(F.Config(**kw), s.size) for s in series]
+    ts = [torch.from_numpy(s).to(dev) for s in series]
+    outs = F.search_batch(plans, ts)
+    for p, t, o in zip(plans, ts, outs):
+        one = F.search(p, t)
+        assert torch.equal(one[: p.n_trials], o[: p.n_trials])
+
+
 @pytest.mark.slow
 def test_survey_workload_sampled(F, orc, dev):
     """2^26 samples at 64 us, 1-30 s, the benchmark's configuration: the whole
