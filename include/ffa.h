@@ -76,6 +76,12 @@ typedef struct {
     int32_t scorer;          /* ffa_scorer: Algorithm 1 (default) or 2           */
     float alg2_window;       /* Algorithm 2 exclusion window as a fraction of the
                                 profile (0 = the paper's 20 %)                     */
+    float clip_sigma;        /* > 0: cap the normalised series at +-clip_sigma
+                                (Section 5's clipping; the int8 code is taken from
+                                the capped value); 0 = off                        */
+    float persist_cutoff;    /* persistence: a sample scores 1 when its normalised
+                                (uncapped) value exceeds this cutoff (Section 5)  */
+    int32_t persistence;     /* nonzero: the plan supports ffa_search_persistence */
 } ffa_search_config;
 
 /* Profile scorer (Section 2.2): Algorithm 1, MAD-normalised boxcars; or
@@ -155,6 +161,18 @@ ffa_status ffa_search_entries(const ffa_plan* plan, const void* d_series, int64_
                               int64_t entry_end, void* d_workspace, size_t workspace_bytes,
                               ffa_record* d_records, int32_t* d_status, void* stream);
 
+/* ffa_search plus the persistence score of Section 5 for every trial:
+ * d_persist[t] (uint32, n_trials of them) = the number of above-cutoff
+ * samples (normalised value > cfg.persist_cutoff, 1/0 per sample) that the
+ * FFA folds into trial t's best boxcar window (the width and phase of its
+ * record): the 0/1 series is folded by the same FFA with integer adds.  A
+ * pulsar spreads such samples over many rows, a single burst contributes at
+ * most its own length.  Needs a plan made with cfg.persistence != 0
+ * (FFA_ERR_ARG otherwise); costs one more integer fold per base period. */
+ffa_status ffa_search_persistence(const ffa_plan* plan, const void* d_series, void* d_workspace,
+                                  size_t workspace_bytes, ffa_record* d_records, uint32_t* d_persist,
+                                  int32_t* d_status, void* stream);
+
 /* A batch of series (e.g. dedispersion trials of uneven length), each with
  * its own plan: series i is searched with plans[i] into d_records[i] (host
  * arrays of `count` pointers).  One workspace, at least the largest plan's
@@ -184,9 +202,117 @@ ffa_status ffa_candidates_entries(const ffa_plan* plan, int64_t entry_begin, int
                                   int32_t* n_out, int64_t* best, int32_t* d_status, void* stream,
                                   int32_t timeout_ms);
 
+/* ---- ffa2best: candidate selection (Section 2.3.3) ------------------------ */
+
+/* Thresholds of ffa2best.  Peak separation: walking the periodogram in trial
+ * (= period) order, a record with S/N >= snr_min starts a candidate, whose
+ * peak is its running maximum; the candidate ends at the first record with
+ * S/N below both peak * (1 - drop_frac) and peak - drop_abs, which may start
+ * the next one.  Grouping (group != 0): a candidate whose S/N times
+ * (1 - group_margin) is at most S * sqrt(d / (d + T |p - q| / q^2)) -- the
+ * expected S/N of a stronger kept candidate (S/N S, period q, duty
+ * d = width / P0) folded at the wrong period p over the observation length
+ * T = n * tsamp, zero once d + T |p - q| / q^2 >= 1 -- is dropped.
+ * Harmonics (primes_max >= 2): a candidate of period p within harm_tol * v
+ * of v = q * (n/x) or v = q / (n/x), for a stronger kept candidate's period
+ * q, a prime x <= primes_max and 0 < n < x, is dropped. */
+typedef struct {
+    double snr_min;       /* baseline S/N                                   */
+    double drop_frac;     /* in [0, 1]                                      */
+    double drop_abs;      /* >= 0                                           */
+    int32_t group;        /* nonzero: group by the smeared response         */
+    int32_t primes_max;   /* 0 or 1: no harmonic matching; at most 97       */
+    double harm_tol;      /* relative tolerance, in [0, 0.1]                */
+    double group_margin;  /* in [0, 1); 0.16 is the paper's largest measured
+                             departure of the algorithms from Eq. 7's law  */
+} ffa2best_config;
+
+/* ffa2best on the whole periodogram d_records (n_trials records of `plan`).
+ * Peaks are found on the device (however many there are); the strongest 4096
+ * of them (all, if fewer) are grouped and harmonic-matched strongest first
+ * (ties: lower periodogram index), each candidate compared only with the
+ * stronger ones kept, and the first min(cap, kept) kept candidates are
+ * written to host `out` (cap in [0, 4096]), strongest first; *n_out receives
+ * their count and *n_peaks the number of peaks found.  Uses the plan's
+ * workspace; enqueues on `stream`, then waits with a bounded wait of
+ * timeout_ms (FFA_ERR_TIMEOUT) and copies the result. */
+ffa_status ffa2best(const ffa_plan* plan, const ffa_record* d_records, const ffa2best_config* cfg,
+                    void* d_workspace, size_t workspace_bytes, ffa_candidate* out, int32_t cap,
+                    int32_t* n_out, int64_t* n_peaks, int32_t* d_status, void* stream,
+                    int32_t timeout_ms);
+
+/* ---- periodogram statistics (Section 4.3, false-alarm analysis) ----------- */
+
+/* Add the S/N histogram of n device records to d_counts (n_bins + 2 uint64
+ * counters, caller-zeroed before the first call, accumulated across calls):
+ * d_counts[0] counts S/N < edges[0], d_counts[1 + b] counts
+ * edges[b] <= S/N < edges[b + 1], d_counts[n_bins + 1] counts
+ * S/N >= edges[n_bins].  edges: host array of n_bins + 1 strictly
+ * increasing floats, 1 <= n_bins <= 4096 (FFA_ERR_ARG otherwise).
+ * Asynchronous on `stream`. */
+ffa_status ffa_snr_histogram(const ffa_record* d_records, int64_t n, const float* edges,
+                             int32_t n_bins, uint64_t* d_counts, void* stream);
+
+/* Gaussian-equivalent sigma of a histogram from ffa_snr_histogram (host
+ * counts): sigma[b] = the z with Q(z) = p_b, Q the upper-tail normal
+ * probability and p_b the fraction of counted trials with S/N >= edges[b],
+ * for b = 0..n_bins (+inf where p_b = 0).  Host only.  FFA_ERR_ARG for an
+ * empty histogram. */
+ffa_status ffa_sigma_gauss(const uint64_t* counts, int32_t n_bins, double* sigma);
+
 /* Wait for `stream` with a bounded wait (polling), then read *d_status.
  * Returns FFA_ERR_TIMEOUT, FFA_ERR_CUDA, the device status, or FFA_OK. */
 ffa_status ffa_wait(void* stream, const int32_t* d_status, int32_t timeout_ms);
+
+/* ---- serving: a request loop with continuous batching --------------------- */
+
+/* A server runs searches submitted from the host as they arrive.  The caller
+ * hands it one block of device memory, the HBM admission budget; each
+ * request needs ffa_server_request_bytes of it (its series, its periodogram
+ * and its search workspace: octave series and fold planes stay on the device
+ * while it runs).  n_slots worker threads, each with its own non-blocking
+ * stream, admit queued requests first-fit in arrival order as slots and
+ * arena memory free up, so requests that arrive while others run overlap on
+ * the device (a request passed over 8 times blocks admission until it fits).
+ * Results are deterministic: a request's records and candidates are the
+ * same alone and in any mix. */
+typedef struct ffa_server ffa_server;
+
+typedef struct {
+    void* d_arena;        /* caller-owned device memory, 256-byte aligned        */
+    size_t arena_bytes;   /* the admission budget                                */
+    int32_t n_slots;      /* searches in flight at once, 1..32                    */
+    int32_t timeout_ms;   /* bounded wait per search (<= 0: 600 s)                */
+} ffa_server_config;
+
+/* Arena bytes one request of n samples with configuration cfg needs. */
+ffa_status ffa_server_request_bytes(const ffa_search_config* cfg, int64_t n, size_t* bytes);
+
+/* Start the worker threads (they use the calling thread's current device). */
+ffa_status ffa_server_create(const ffa_server_config* cfg, ffa_server** out);
+
+/* Queue a search of the n-sample host series (pinned memory lets its copy
+ * overlap other requests' work; it must stay valid until the request
+ * completes).  On completion the server keeps the top_k (<= 4096) candidates
+ * with S/N >= snr_min, the best trial, and, if host_records is non-null,
+ * copies the whole periodogram there (n_trials records).  *ticket identifies
+ * the request.  FFA_ERR_OOM if the request needs more than the whole arena. */
+ffa_status ffa_server_submit(ffa_server* server, const ffa_search_config* cfg, const void* host_series,
+                             int64_t n, double snr_min, int32_t top_k, ffa_record* host_records,
+                             int64_t* ticket);
+
+/* Wait up to timeout_ms (< 0: forever) for a request, copy up to cap of its
+ * candidates to `out`, its best trial to *best, and times_ms[0..2] = queued,
+ * running and total (latency) milliseconds; then forget the ticket.  Returns
+ * the request's own status (FFA_ERR_TIMEOUT leaves the ticket valid). */
+ffa_status ffa_server_wait(ffa_server* server, int64_t ticket, int32_t timeout_ms, ffa_candidate* out,
+                           int32_t cap, int32_t* n_out, int64_t* best, double* times_ms);
+
+/* Requests waiting, requests running, arena bytes in use. */
+ffa_status ffa_server_stats(ffa_server* server, int64_t* queued, int64_t* in_flight, size_t* arena_used);
+
+/* Finish every submitted request, stop the workers and free the server. */
+void ffa_server_destroy(ffa_server* server);
 
 /* ---- individual steps (for step-level parity checks) ----------------------- */
 

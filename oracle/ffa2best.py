@@ -84,26 +84,40 @@ def harmonic(p: float, q: float, primes_max: int, tol: float) -> bool:
     return False
 
 
+def fractions(primes_max: int) -> np.ndarray:
+    """R20's fractions n/x, 0 < n < x, for every prime x <= primes_max."""
+    return np.array([n / x for x in primes_upto(primes_max) for n in range(1, x)], np.float64)
+
+
 def select(snr, periods, delta, t_obs: float, group: bool, primes_max: int, tol: float,
            order=None, cap: int | None = None, margin: float = 0.16) -> list[int]:
     """R19-R21 over a candidate list: indices into snr/periods/delta, kept
-    ones strongest first.  `order` restricts the list (default: all)."""
+    ones strongest first.  `order` restricts the list (default: all).  Each
+    candidate is tested against every kept one at once (numpy elementwise,
+    the same binary64 operations as smeared() and harmonic())."""
     idx = list(range(len(snr))) if order is None else list(order)
     idx.sort(key=lambda i: (-float(snr[i]), i))
     shrink = 1.0 - margin
+    fr = fractions(primes_max) if primes_max >= 2 else np.zeros(0)
+    kq = np.zeros(len(idx))
+    ks = np.zeros(len(idx))
+    kd = np.zeros(len(idx))
     kept: list[int] = []
     for i in idx:
-        p = float(periods[i])
+        p, s = float(periods[i]), float(snr[i])
+        nk = len(kept)
         drop = False
-        for j in kept:
-            q = float(periods[j])
-            if group and float(snr[i]) * shrink <= smeared(float(snr[j]), float(delta[j]), p, q, t_obs):
-                drop = True
-            elif primes_max >= 2 and harmonic(p, q, primes_max, tol):
-                drop = True
-            if drop:
-                break
+        if nk:
+            q, sj, dj = kq[:nk], ks[:nk], kd[:nk]
+            if group:
+                de = dj + t_obs * np.abs(p - q) / (q * q)
+                resp = np.where(de >= 1.0, 0.0, sj * np.sqrt(dj / de))
+                drop = bool(np.any(s * shrink <= resp))
+            if not drop and fr.size:
+                v = np.concatenate([q[:, None] * fr[None, :], q[:, None] / fr[None, :]], axis=1)
+                drop = bool(np.any(np.abs(p - v) <= tol * v))
         if not drop:
+            kq[nk], ks[nk], kd[nk] = p, s, float(delta[i])
             kept.append(i)
             if cap is not None and len(kept) == cap:
                 break

@@ -4,7 +4,27 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/ffa.h"
+
+// The search plan (host only): base periods in periodogram order, per-octave
+// bookkeeping and the byte offsets of the workspace regions.
+struct ffa_plan {
+    ffa_search_config cfg;
+    int64_t n = 0;       // input samples
+    int64_t n0 = 0;      // after pre-downsampling
+    int32_t window = 1;  // odd running-median window (1 = off)
+    int32_t n_octaves = 0;
+    int64_t n_trials = 0;
+    int64_t max_plane = 0;  // largest m_rows * p0
+    std::vector<ffa_plan_entry> entries;
+    std::vector<int64_t> oct_first, oct_count, oct_n;
+    // workspace layout (bytes)
+    size_t off_raw_a = 0, off_raw_b = 0, off_resid = 0, off_z = 0, off_stats = 0, off_plane0 = 0,
+           off_plane1 = 0, off_cand = 0, off_best = 0, off_bits = 0, ws_bytes = 0;
+};
+
 
 namespace ffa {
 
@@ -23,8 +43,16 @@ ffa_status launch_downsample(const void* d_in, int32_t in_type, int64_t n, int64
                              double* d_out, cudaStream_t st);
 ffa_status launch_detrend(const double* d_raw, int64_t n, int32_t window, double* d_resid,
                           int32_t* d_status, cudaStream_t st);
+// clip > 0 caps the normalised series at +-clip; d_bits (optional) receives
+// z > cutoff per sample (1/0, before the cap).
 ffa_status launch_normalise(const double* d_resid, int64_t n, int32_t precision, void* d_out,
-                            double* d_stats, cudaStream_t st);
+                            double* d_stats, cudaStream_t st, float clip = 0.0f,
+                            float cutoff = 0.0f, int8_t* d_bits = nullptr);
+// Persistence (Section 5) of `count` trials: d_bplane is the folded 0/1
+// series after all but the last FFA stage (m_rows rows of p0, int32); each
+// trial's sum over its record's best window, last stage applied on the fly.
+ffa_status launch_persist(const int32_t* d_bplane, int64_t m_rows, int64_t p0,
+                          const ffa_record* d_rec, uint32_t* d_persist, cudaStream_t st);
 ffa_status launch_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
                        int64_t m_rows, int stages, void* d_plane, void* d_tmp, cudaStream_t st);
 // Algorithm 1 on `count` trials starting at trial0.  fused: d_prof is the
@@ -37,6 +65,9 @@ ffa_status launch_score2(const void* d_prof, int32_t precision, bool fused, int6
 ffa_status launch_score_alg2(const void* d_prof, int32_t precision, bool fused, int64_t count,
                              int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
                              float excl_frac, ffa_record* d_rec, cudaStream_t st);
+
+// ffa2best on a plan's records (defined in best.cu); workspace bytes it needs.
+size_t best_workspace_bytes(int64_t n_entries, int64_t n_trials);
 
 constexpr int STATS_DOUBLES = 2 + 1024;  // {mean, std} + reduction partials
 

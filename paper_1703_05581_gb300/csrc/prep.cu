@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -525,22 +527,31 @@ __global__ void __launch_bounds__(NRM_BLOCKS) k_stats_final(int64_t n, int mode,
     }
 }
 
+// z = (r - mean) / sd in FP64 (0 for a constant series); bits[i] = z > cutoff
+// (uncapped) when bits is given; then the cap z = min(max(z, -clip), clip)
+// (clip = +inf when off) before the FP32 rounding or the int8 code.
 __global__ void k_normalise_f32(const double* __restrict__ r, int64_t n, const double* stats,
+                                double clip, double cutoff, int8_t* __restrict__ bits,
                                 float* __restrict__ z) {
     double mean = stats[0], sd = stats[1];
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         double v = sd > 0.0 ? __ddiv_rn(r[i] - mean, sd) : 0.0;
+        if (bits) bits[i] = v > cutoff ? 1 : 0;
+        v = fmin(fmax(v, -clip), clip);
         z[i] = __double2float_rn(v);
     }
 }
 
 __global__ void k_normalise_i8(const double* __restrict__ r, int64_t n, const double* stats,
+                               double clip, double cutoff, int8_t* __restrict__ bits,
                                int8_t* __restrict__ q) {
     double mean = stats[0], sd = stats[1];
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         double v = sd > 0.0 ? __ddiv_rn(r[i] - mean, sd) : 0.0;
+        if (bits) bits[i] = v > cutoff ? 1 : 0;
+        v = fmin(fmax(v, -clip), clip);
         double c = rint(16.0 * v);
         c = c > 127.0 ? 127.0 : (c < -127.0 ? -127.0 : c);
         q[i] = (int8_t)(int)c;
@@ -548,17 +559,21 @@ __global__ void k_normalise_i8(const double* __restrict__ r, int64_t n, const do
 }
 
 ffa_status launch_normalise(const double* d_resid, int64_t n, int32_t precision, void* d_out,
-                            double* d_stats, cudaStream_t st) {
+                            double* d_stats, cudaStream_t st, float clip, float cutoff,
+                            int8_t* d_bits) {
     if (n <= 0) return FFA_OK;
+    const double cl = clip > 0.0f ? (double)clip : INFINITY;
     double* partial = d_stats + 2;
     k_stats_partial<<<NRM_BLOCKS, NRM_THREADS, 0, st>>>(d_resid, n, d_stats, 0, partial);
     k_stats_final<<<1, NRM_BLOCKS, 0, st>>>(n, 0, d_stats, partial);
     k_stats_partial<<<NRM_BLOCKS, NRM_THREADS, 0, st>>>(d_resid, n, d_stats, 1, partial);
     k_stats_final<<<1, NRM_BLOCKS, 0, st>>>(n, 1, d_stats, partial);
     if (precision == FFA_FOLD_F32)
-        k_normalise_f32<<<grid_for(n, 256), 256, 0, st>>>(d_resid, n, d_stats, (float*)d_out);
+        k_normalise_f32<<<grid_for(n, 256), 256, 0, st>>>(d_resid, n, d_stats, cl, (double)cutoff,
+                                                          d_bits, (float*)d_out);
     else
-        k_normalise_i8<<<grid_for(n, 256), 256, 0, st>>>(d_resid, n, d_stats, (int8_t*)d_out);
+        k_normalise_i8<<<grid_for(n, 256), 256, 0, st>>>(d_resid, n, d_stats, cl, (double)cutoff,
+                                                         d_bits, (int8_t*)d_out);
     FFA_LAUNCH_CHECK("k_normalise");
     count_launch(5);
     return FFA_OK;

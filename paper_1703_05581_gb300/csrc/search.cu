@@ -20,21 +20,6 @@
 #include "common.cuh"
 #include "internal.h"
 
-struct ffa_plan {
-    ffa_search_config cfg;
-    int64_t n = 0;       // input samples
-    int64_t n0 = 0;      // after pre-downsampling
-    int32_t window = 1;  // odd running-median window (1 = off)
-    int32_t n_octaves = 0;
-    int64_t n_trials = 0;
-    int64_t max_plane = 0;  // largest m_rows * p0
-    std::vector<ffa_plan_entry> entries;
-    std::vector<int64_t> oct_first, oct_count, oct_n;
-    // workspace layout (bytes)
-    size_t off_raw_a = 0, off_raw_b = 0, off_resid = 0, off_z = 0, off_stats = 0, off_plane0 = 0,
-           off_plane1 = 0, off_cand = 0, ws_bytes = 0;
-};
-
 namespace ffa {
 
 namespace {
@@ -311,6 +296,10 @@ ffa_status ffa_plan_create(const ffa_search_config* cfg, int64_t n, ffa_plan** o
         return fail(FFA_ERR_ARG, "plan: bad scorer");
     if (!(cfg->alg2_window >= 0.0f && cfg->alg2_window < 1.0f))
         return fail(FFA_ERR_ARG, "plan: alg2_window must be in [0, 1)");
+    if (!(cfg->clip_sigma >= 0.0f) || std::isinf(cfg->clip_sigma))
+        return fail(FFA_ERR_ARG, "plan: clip_sigma must be finite and >= 0");
+    if (cfg->persistence && !std::isfinite(cfg->persist_cutoff))
+        return fail(FFA_ERR_ARG, "plan: persist_cutoff must be finite");
     if (cfg->n_widths_fixed < 0 || cfg->n_widths_fixed > 16)
         return fail(FFA_ERR_ARG, "plan: n_widths_fixed must be in [0, 16]");
     if (cfg->n_widths_fixed == 0 && !(cfg->duty_max > 0.0))
@@ -418,6 +407,10 @@ ffa_status ffa_plan_create(const ffa_search_config* cfg, int64_t n, ffa_plan** o
     p->off_cand = off;
     off = align256(off + sizeof(CandCtl) + 256 + sizeof(unsigned long long) * CAND_MAX +
                    sizeof(CandOut) * CAND_MAX);
+    p->off_best = off;
+    off = align256(off + ffa::best_workspace_bytes((int64_t)p->entries.size(), p->n_trials));
+    p->off_bits = off;
+    if (cfg->persistence) off = align256(off + (size_t)n0);
     p->ws_bytes = off;
     *out = p;
     return FFA_OK;
@@ -448,7 +441,7 @@ ffa_status ffa_plan_entries(const ffa_plan* p, ffa_plan_entry* out, int64_t cap)
 // folded and scored.
 static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_ws, size_t ws_bytes,
                                ffa_record* d_records, int32_t* d_status, cudaStream_t st, int64_t e0,
-                               int64_t e1) {
+                               int64_t e1, uint32_t* d_persist = nullptr) {
     if (!p) return fail(FFA_ERR_ARG, "search: null plan");
     const int64_t ne = (int64_t)p->entries.size();
     if (e0 < 0 || e1 > ne || e0 > e1) return fail(FFA_ERR_ARG, "search: entry range out of bounds");
@@ -461,6 +454,7 @@ static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_
     double* resid = (double*)(ws + p->off_resid);
     void* z = ws + p->off_z;
     double* stats = (double*)(ws + p->off_stats);
+    int8_t* bits = d_persist ? (int8_t*)(ws + p->off_bits) : nullptr;
     void* plane0 = ws + p->off_plane0;
     void* plane1 = ws + p->off_plane1;
     const ffa_search_config& c = p->cfg;
@@ -486,7 +480,8 @@ static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_
             s = e == cudaSuccess ? FFA_OK : cuda_fail(e, "search: copy");
         }
         if (s != FFA_OK) return s;
-        s = launch_normalise(resid, n_o, c.precision, z, stats, st);
+        s = launch_normalise(resid, n_o, c.precision, z, stats, st, c.clip_sigma, c.persist_cutoff,
+                             bits);
         if (s != FFA_OK) return s;
         prep_t.stop();
         PhaseTimer fold_t(1, o, st);
@@ -517,10 +512,29 @@ static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_
                                   d_records + e.first_trial, d_status, st);
             if (s != FFA_OK) return s;
             score_k.stop();
+            if (d_persist) {
+                // the 0/1 series through the same fold, then each trial's window sum
+                s = launch_fold(bits, FFA_FOLD_I8, e.p0, e.m_data, e.m_rows, m > 0 ? m - 1 : 0,
+                                plane0, plane1, st);
+                if (s != FFA_OK) return s;
+                s = launch_persist((const int32_t*)plane0, e.m_rows, e.p0, d_records + e.first_trial,
+                                   d_persist + e.first_trial, st);
+                if (s != FFA_OK) return s;
+            }
         }
         fold_t.stop();
     }
     return FFA_OK;
+}
+
+ffa_status ffa_search_persistence(const ffa_plan* p, const void* d_series, void* d_ws,
+                                  size_t ws_bytes, ffa_record* d_records, uint32_t* d_persist,
+                                  int32_t* d_status, void* stream) {
+    if (!p) return fail(FFA_ERR_ARG, "search_persistence: null plan");
+    if (!p->cfg.persistence) return fail(FFA_ERR_ARG, "search_persistence: plan made without persistence");
+    if (p->n_trials > 0 && !d_persist) return fail(FFA_ERR_ARG, "search_persistence: null output");
+    return search_range(p, d_series, d_ws, ws_bytes, d_records, d_status, as_stream(stream), 0,
+                        (int64_t)p->entries.size(), d_persist);
 }
 
 ffa_status ffa_search(const ffa_plan* p, const void* d_series, void* d_ws, size_t ws_bytes,

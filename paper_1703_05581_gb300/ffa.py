@@ -41,7 +41,8 @@ class SearchConfig(C.Structure):
                 ("downsample0", C.c_int32), ("detrend_window", C.c_int32),
                 ("min_rows", C.c_int32), ("in_type", C.c_int32), ("precision", C.c_int32),
                 ("n_widths_fixed", C.c_int32), ("widths_fixed", C.c_int32 * 16),
-                ("scorer", C.c_int32), ("alg2_window", C.c_float)]
+                ("scorer", C.c_int32), ("alg2_window", C.c_float), ("clip_sigma", C.c_float),
+                ("persist_cutoff", C.c_float), ("persistence", C.c_int32)]
 
 
 class Record(C.Structure):
@@ -59,6 +60,17 @@ class Candidate(C.Structure):
     _fields_ = [("trial", C.c_int64), ("period_s", C.c_double), ("snr", C.c_float),
                 ("octave", C.c_int32), ("p0", C.c_int32), ("k", C.c_int32),
                 ("width", C.c_int32), ("phase", C.c_int32)]
+
+
+class BestConfig(C.Structure):
+    _fields_ = [("snr_min", C.c_double), ("drop_frac", C.c_double), ("drop_abs", C.c_double),
+                ("group", C.c_int32), ("primes_max", C.c_int32), ("harm_tol", C.c_double),
+                ("group_margin", C.c_double)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("d_arena", C.c_void_p), ("arena_bytes", C.c_size_t), ("n_slots", C.c_int32),
+                ("timeout_ms", C.c_int32)]
 
 
 RECORD_DTYPE = np.dtype([("snr", "<f4"), ("width", "<i4"), ("phase", "<i4"), ("flags", "<u4")])
@@ -80,11 +92,22 @@ _sig = {
     "ffa_plan_entries": ([_P, _P, _i64], C.c_int),
     "ffa_search": ([_P, _P, _P, C.c_size_t, _P, _P, _P], C.c_int),
     "ffa_search_entries": ([_P, _P, _i64, _i64, _P, C.c_size_t, _P, _P, _P], C.c_int),
+    "ffa_search_persistence": ([_P, _P, _P, C.c_size_t, _P, _P, _P, _P], C.c_int),
     "ffa_search_batch": ([_P, _P, _i32, _P, C.c_size_t, _P, _P, _P], C.c_int),
     "ffa_candidates": ([_P, _P, C.c_double, _i32, _P, C.c_size_t, _P, _P, _P, _P, _P, _i32],
                        C.c_int),
     "ffa_candidates_entries": ([_P, _i64, _i64, _P, C.c_double, _i32, _P, C.c_size_t, _P, _P, _P, _P,
                                 _P, _i32], C.c_int),
+    "ffa2best": ([_P, _P, C.POINTER(BestConfig), _P, C.c_size_t, _P, _i32, _P, _P, _P, _P, _i32],
+                 C.c_int),
+    "ffa_snr_histogram": ([_P, _i64, _P, _i32, _P, _P], C.c_int),
+    "ffa_sigma_gauss": ([_P, _i32, _P], C.c_int),
+    "ffa_server_request_bytes": ([C.POINTER(SearchConfig), _i64, _P], C.c_int),
+    "ffa_server_create": ([C.POINTER(ServerConfig), C.POINTER(C.c_void_p)], C.c_int),
+    "ffa_server_submit": ([_P, C.POINTER(SearchConfig), _P, _i64, C.c_double, _i32, _P, _P], C.c_int),
+    "ffa_server_wait": ([_P, _i64, _i32, _P, _i32, _P, _P, _P], C.c_int),
+    "ffa_server_stats": ([_P, _P, _P, _P], C.c_int),
+    "ffa_server_destroy": ([_P], None),
     "ffa_wait": ([_P, _P, _i32], C.c_int),
     "ffa_downsample": ([_P, _i32, _i64, _i64, _P, _P], C.c_int),
     "ffa_detrend": ([_P, _i64, _i32, _P, _P, _P], C.c_int),
@@ -138,6 +161,9 @@ class Config:
     widths: tuple = field(default_factory=tuple)
     scorer: int = SCORE_ALG1
     alg2_window: float = 0.0
+    clip_sigma: float = 0.0
+    persist_cutoff: float = 0.0
+    persistence: bool = False
 
     def c(self) -> SearchConfig:
         c = SearchConfig()
@@ -150,6 +176,8 @@ class Config:
         for i, w in enumerate(self.widths):
             c.widths_fixed[i] = int(w)
         c.scorer, c.alg2_window = self.scorer, self.alg2_window
+        c.clip_sigma, c.persist_cutoff = self.clip_sigma, self.persist_cutoff
+        c.persistence = int(bool(self.persistence))
         return c
 
 
@@ -215,6 +243,21 @@ def search(plan: Plan, series: torch.Tensor, workspace: torch.Tensor | None = No
     return records
 
 
+def search_persistence(plan: Plan, series: torch.Tensor, workspace: torch.Tensor | None = None,
+                       records: torch.Tensor | None = None, persist: torch.Tensor | None = None,
+                       status: torch.Tensor | None = None, stream=None):
+    """ffa_search plus the per-trial persistence score: (records, persist)."""
+    dev = series.device
+    workspace = plan.workspace(dev) if workspace is None else workspace
+    records = plan.records(dev) if records is None else records
+    if persist is None:
+        persist = torch.zeros(max(plan.n_trials, 1), dtype=torch.int32, device=dev)
+    status = status_word(dev) if status is None else status
+    _check(_lib.ffa_search_persistence(plan._h, _ptr(series), _ptr(workspace), workspace.numel(),
+                                       _ptr(records), _ptr(persist), _ptr(status), _stream(stream)))
+    return records, persist
+
+
 def search_entries(plan: Plan, series: torch.Tensor, entry_begin: int, entry_end: int,
                    workspace: torch.Tensor | None = None, records: torch.Tensor | None = None,
                    status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
@@ -277,6 +320,117 @@ def candidates_entries(plan: Plan, entry_begin: int, entry_end: int, records: to
                                        out.ctypes.data_as(C.c_void_p), C.byref(n_out), C.byref(best),
                                        _ptr(status), _stream(stream), int(timeout_ms)))
     return out[: n_out.value], best.value
+
+
+def ffa2best(plan: Plan, records: torch.Tensor, workspace: torch.Tensor, snr_min: float,
+             drop_frac: float = 0.1, drop_abs: float = 0.5, group: bool = True,
+             primes_max: int = 31, harm_tol: float = 1e-5, group_margin: float = 0.16,
+             cap: int = 256, status: torch.Tensor | None = None, stream=None,
+             timeout_ms: int = 600000):
+    """Candidate selection of Section 2.3.3 on the device periodogram: returns
+    (kept candidates strongest first, number of periodogram peaks found)."""
+    status = status_word(records.device) if status is None else status
+    cfg = BestConfig(float(snr_min), float(drop_frac), float(drop_abs), int(bool(group)),
+                     int(primes_max), float(harm_tol), float(group_margin))
+    out = np.zeros(max(cap, 1), CANDIDATE_DTYPE)
+    n_out, n_peaks = C.c_int32(), C.c_int64()
+    _check(_lib.ffa2best(plan._h, _ptr(records), C.byref(cfg), _ptr(workspace), workspace.numel(),
+                         out.ctypes.data_as(C.c_void_p), int(cap), C.byref(n_out), C.byref(n_peaks),
+                         _ptr(status), _stream(stream), int(timeout_ms)))
+    return out[: n_out.value], n_peaks.value
+
+
+def snr_histogram(records: torch.Tensor, n: int, edges, counts: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """Add the S/N histogram of the first n records to `counts` (int64 device
+    tensor of len(edges) + 1 counters: below, each bin, at/above the top)."""
+    e = np.ascontiguousarray(edges, dtype=np.float32)
+    if counts is None:
+        counts = torch.zeros(e.size + 1, dtype=torch.int64, device=records.device)
+    _check(_lib.ffa_snr_histogram(_ptr(records), int(n), e.ctypes.data_as(C.c_void_p), e.size - 1,
+                                  _ptr(counts), _stream(stream)))
+    return counts
+
+
+def sigma_gauss(counts) -> np.ndarray:
+    """Gaussian-equivalent sigma at each histogram edge (host counts)."""
+    c = np.ascontiguousarray(counts, dtype=np.uint64)
+    out = np.zeros(c.size - 1)
+    _check(_lib.ffa_sigma_gauss(c.ctypes.data_as(C.c_void_p), c.size - 2,
+                                out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def request_bytes(cfg: Config, n: int) -> int:
+    b = C.c_size_t()
+    c = cfg.c()
+    _check(_lib.ffa_server_request_bytes(C.byref(c), int(n), C.byref(b)))
+    return b.value
+
+
+class Server:
+    """Continuous-batching request loop (ffa_server_*): `arena_bytes` of device
+    memory is the admission budget, `n_slots` searches run at once."""
+
+    def __init__(self, arena_bytes: int, n_slots: int = 4, device=None, timeout_ms: int = 600000):
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=dev)
+        cfg = ServerConfig(C.c_void_p(self.arena.data_ptr()), int(arena_bytes), int(n_slots),
+                           int(timeout_ms))
+        h = C.c_void_p()
+        with torch.cuda.device(dev):
+            _check(_lib.ffa_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._keep = {}  # ticket -> host buffers that must outlive the request
+
+    def submit(self, cfg: Config, series: np.ndarray, snr_min: float = 6.0, top_k: int = 16,
+               records: bool = False) -> int:
+        x = np.ascontiguousarray(series)
+        c = cfg.c()
+        rec = None
+        if records:
+            rec = np.zeros(max(Plan(cfg, x.size).n_trials, 1), RECORD_DTYPE)
+        t = C.c_int64()
+        _check(_lib.ffa_server_submit(self._h, C.byref(c), x.ctypes.data_as(C.c_void_p), x.size,
+                                      float(snr_min), int(top_k),
+                                      None if rec is None else rec.ctypes.data_as(C.c_void_p),
+                                      C.byref(t)))
+        self._keep[t.value] = (x, c, rec, top_k)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """Return (candidates, best, records or None, times_ms [queued, running, total])."""
+        x, c, rec, top_k = self._keep[ticket]
+        out = np.zeros(max(top_k, 1), CANDIDATE_DTYPE)
+        n_out, best = C.c_int32(), C.c_int64()
+        times = np.zeros(3)
+        try:
+            _check(_lib.ffa_server_wait(self._h, int(ticket), int(timeout_ms),
+                                        out.ctypes.data_as(C.c_void_p), int(top_k), C.byref(n_out),
+                                        C.byref(best), times.ctypes.data_as(C.c_void_p)))
+        except FFAError as e:
+            if e.status != ERR_TIMEOUT:
+                self._keep.pop(ticket, None)
+            raise
+        self._keep.pop(ticket, None)
+        return out[: n_out.value], best.value, rec, times
+
+    def stats(self):
+        q, f, u = C.c_int64(), C.c_int64(), C.c_size_t()
+        _check(_lib.ffa_server_stats(self._h, C.byref(q), C.byref(f), C.byref(u)))
+        return q.value, f.value, u.value
+
+    def close(self) -> None:
+        if self._h:
+            _lib.ffa_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def wait(status: torch.Tensor | None = None, stream=None, timeout_ms: int = 600000) -> None:

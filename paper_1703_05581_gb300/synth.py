@@ -111,6 +111,17 @@ SURVEY = dict(n=1 << 26, tsamp=64e-6, period_min_s=1.0, period_max_s=30.0, duty=
               seed=2)
 
 
+# False-alarm statistics (Section 4.3): 26 white-noise series of the survey's
+# shape searched from 1 to 20 s at D0 = 32, about 10^8 trials in all.
+NOISE = dict(n=1 << 26, tsamp=64e-6, downsample0=32, period_min_s=1.0, period_max_s=20.0,
+             n_series=26, seed=100)
+
+
+def white_series(seed: int, n: int = NOISE["n"]) -> np.ndarray:
+    """N(0, 1) float32 samples (the noise-only series of the false-alarm workload)."""
+    return make_series(SeriesSpec(n=n, seed=seed))
+
+
 def plain_series(seed: int = PLAIN["seed"], n: int = PLAIN["n"]) -> np.ndarray:
     """White noise + 0.8 s Gaussian pulsar (3 % FWHM, S/N 15) sampled at 2.048 ms."""
     p = PLAIN["pulsar_period_s"] / PLAIN["tsamp"]

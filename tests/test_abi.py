@@ -23,7 +23,7 @@ def declared_functions():
         if fn.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", fn)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"^[A-Za-z_][\w \*]*?\b(ffa_\w+)\s*\(", txt, flags=re.M))
+            names |= set(re.findall(r"^[A-Za-z_][\w \*]*?\b(ffa\w+)\s*\(", txt, flags=re.M))
     return sorted(names)
 
 
@@ -35,6 +35,25 @@ def test_exports_every_declared_symbol(ffa):
     for n in names:
         assert hasattr(lib, n), n
     assert set(names) <= set(ffa.EXPORTS) | {"ffa_plan_destroy"}
+
+
+def test_sigma_gauss_host(ffa):
+    """The histogram-to-sigma mapping (host only) against scipy's normal
+    quantile: sigma at each edge = Q^-1(fraction of trials at or above it)."""
+    sp = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        c = rng.integers(0, 10**6, size=int(rng.integers(3, 60))).astype(np.uint64)
+        c[-1] = max(int(c[-1]), 1)
+        got = ffa.sigma_gauss(c)
+        tail = np.cumsum(c[::-1].astype(np.float64))[::-1][1:] / float(c.sum())
+        assert np.allclose(got, -sp.ndtri(tail), rtol=0, atol=1e-9)
+    # an empty top bin maps to +inf; one trial in 10^12 is 7.03 sigma
+    c = np.array([0, 10**12 - 1, 1, 0], np.uint64)
+    got = ffa.sigma_gauss(c)
+    assert got[-1] == np.inf and abs(got[1] - 7.034483825) < 1e-6
+    with pytest.raises(ffa.FFAError):
+        ffa.sigma_gauss(np.zeros(4, np.uint64))
 
 
 def test_status_strings(ffa):
