@@ -32,7 +32,7 @@ def upper_tail(sigma: float) -> float:
 
 
 def run(n_series: int = synth.NOISE["n_series"], n: int = synth.NOISE["n"],
-        scorer: int = ffa.SCORE_ALG1, sigmas=(3.0, 4.0, 5.0), seed0: int = synth.NOISE["seed"],
+        scorer: int = ffa.SCORE_ALG1, sigmas=(4.0, 5.0), seed0: int = synth.NOISE["seed"],
         dev=None, edges=EDGES, series=None) -> dict:
     """Search n_series white-noise series; return the histogram, the sigma of
     each edge and the exact S/N at each requested sigma."""
