@@ -75,7 +75,6 @@ struct BestEntry {
 };
 
 struct WalkArgs {
-    float lo_f;      // smallest float >= lo: s < lo  <=>  s < lo_f
     float base_f;    // smallest float >= snr_min
     double keep;     // 1 - drop_frac
     double drop_abs;
@@ -235,7 +234,10 @@ struct WalkState {
     bool inside;
     float pk;
     uint32_t pi;
-    double pk_keep, pk_abs;  // pk * (1 - drop_frac), pk - drop_abs
+    // the end test s < pk * (1 - drop_frac) && s < pk - drop_abs, both sides
+    // FP64, as one float compare: for a float s, s < d exactly when s is below
+    // the smallest float >= d (d rounded towards +inf)
+    float end_below;
 };
 
 constexpr unsigned long long OUTSIDE = ~0ull;
@@ -248,8 +250,8 @@ __device__ __forceinline__ void set_peak(WalkState& w, float pk, uint32_t pi, co
     w.inside = true;
     w.pk = pk;
     w.pi = pi;
-    w.pk_keep = __dmul_rn((double)pk, a.keep);
-    w.pk_abs = __dsub_rn((double)pk, a.drop_abs);
+    const double t = fmin(__dmul_rn((double)pk, a.keep), __dsub_rn((double)pk, a.drop_abs));
+    w.end_below = __double2float_ru(t);
 }
 
 __device__ __forceinline__ WalkState decode(unsigned long long e, const WalkArgs& a) {
@@ -257,22 +259,19 @@ __device__ __forceinline__ WalkState decode(unsigned long long e, const WalkArgs
     w.inside = false;
     w.pk = 0.0f;
     w.pi = 0;
-    w.pk_keep = w.pk_abs = 0.0;
+    w.end_below = 0.0f;
     if (e != OUTSIDE) set_peak(w, fkey_inv((uint32_t)(e >> 32)), (uint32_t)(e & 0xffffffffull), a);
     return w;
 }
 
 // The state machine over records [b, lim), lim - b <= 32, one warp
-// (warp-uniform state; lane j holds record b + j).  EMIT: report the peak of
-// every candidate that ends here.
+// (warp-uniform state; lane j holds record b + j's S/N in s).  EMIT: report
+// the peak of every candidate that ends here.
 template <bool EMIT>
-__device__ __forceinline__ void walk_batch(const ffa_record* __restrict__ rec, int64_t b, int64_t lim,
-                                           const WalkArgs& a, WalkState& w, BestCtl* ctl,
-                                           unsigned long long* peaks, uint32_t* hist, const WalkMode& md,
-                                           int lane) {
-    const int64_t i = b + lane;
-    const bool valid = i < lim;
-    const float s = valid ? rec[i].snr : 0.0f;
+__device__ __forceinline__ void walk_batch(float s, int64_t b, int64_t lim, const WalkArgs& a, WalkState& w,
+                                           BestCtl* ctl, unsigned long long* peaks, uint32_t* hist,
+                                           const WalkMode& md, int lane) {
+    const bool valid = b + lane < lim;
     const unsigned starts = __ballot_sync(0xffffffffu, valid && s >= a.base_f);
     if (!w.inside && !starts) return;
     const int nvalid = (int)min((int64_t)32, lim - b);
@@ -281,13 +280,17 @@ __device__ __forceinline__ void walk_batch(const ffa_record* __restrict__ rec, i
         if (w.inside) {
             if (sj > w.pk) {
                 set_peak(w, sj, (uint32_t)(b + j), a);
-            } else if ((double)sj < w.pk_keep && (double)sj < w.pk_abs) {
+            } else if (sj < w.end_below) {
                 if (EMIT) emit_peak(ctl, peaks, hist, md, w.pk, w.pi, lane);
                 w.inside = false;
             }
         }
         if (!w.inside && sj >= a.base_f) set_peak(w, sj, (uint32_t)(b + j), a);
     }
+}
+
+__device__ __forceinline__ float snr_at(const ffa_record* __restrict__ rec, int64_t i, int64_t lim) {
+    return i < lim ? rec[i].snr : 0.0f;
 }
 
 __device__ __forceinline__ WalkMode load_mode(int first, const BestCtl* ctl) {
@@ -319,9 +322,12 @@ __global__ void __launch_bounds__(256) k_best_spec(const ffa_record* __restrict_
     for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += n_warps) {
         const int64_t c0 = c * WALK_CHUNK, c1 = min(n, c0 + WALK_CHUNK);
         WalkState w = decode(OUTSIDE, a);
+        float s = snr_at(rec, c0 + lane, c1);
         for (int64_t b = c0; b < c1; b += 32) {
+            const float sn = snr_at(rec, b + 32 + lane, c1);  // next batch, in flight meanwhile
             if (lane == 0) ck[b >> 5] = encode(w);
-            walk_batch<false>(rec, b, c1, a, w, nullptr, nullptr, nullptr, none, lane);
+            walk_batch<false>(s, b, c1, a, w, nullptr, nullptr, nullptr, none, lane);
+            s = sn;
         }
         if (lane == 0) end_state[c] = encode(w);
     }
@@ -347,10 +353,17 @@ __global__ void __launch_bounds__(32) k_best_fix(const ffa_record* __restrict__ 
         const int64_t c0 = c * WALK_CHUNK, c1 = min(n, c0 + WALK_CHUNK);
         const int32_t nb = (int32_t)((c1 - c0 + 31) >> 5);
         int32_t t = 0;
+        float s = snr_at(rec, c0 + lane, c1);
+        unsigned long long cke = ck[c0 >> 5];
         for (; t < nb; ++t) {
             const int64_t b = c0 + 32 * (int64_t)t;
-            if (encode(w) == ck[b >> 5]) break;
-            walk_batch<true>(rec, b, c1, a, w, ctl, peaks, hist, md, lane);
+            if (encode(w) == cke) break;
+            // the next batch's values and checkpoint, in flight meanwhile
+            const float sn = snr_at(rec, b + 32 + lane, c1);
+            const unsigned long long ckn = t + 1 < nb ? ck[(b >> 5) + 1] : OUTSIDE;
+            walk_batch<true>(s, b, c1, a, w, ctl, peaks, hist, md, lane);
+            s = sn;
+            cke = ckn;
         }
         if (lane == 0) merge[c] = t;
         if (t < nb) w = decode(end_state[c], a);
@@ -375,7 +388,12 @@ __global__ void __launch_bounds__(256) k_best_tail(const ffa_record* __restrict_
         const int64_t b0 = c0 + 32 * (int64_t)merge[c];
         if (b0 >= c1) continue;
         WalkState w = decode(ck[b0 >> 5], a);
-        for (int64_t b = b0; b < c1; b += 32) walk_batch<true>(rec, b, c1, a, w, ctl, peaks, hist, md, lane);
+        float s = snr_at(rec, b0 + lane, c1);
+        for (int64_t b = b0; b < c1; b += 32) {
+            const float sn = snr_at(rec, b + 32 + lane, c1);
+            walk_batch<true>(s, b, c1, a, w, ctl, peaks, hist, md, lane);
+            s = sn;
+        }
     }
 }
 
@@ -653,13 +671,11 @@ extern "C" ffa_status ffa2best(const ffa_plan* p, const ffa_record* d_records,
     WalkArgs wa;
     wa.keep = 1.0 - cfg->drop_frac;
     wa.drop_abs = cfg->drop_abs;
-    const double lo = std::min(cfg->snr_min * wa.keep, cfg->snr_min - cfg->drop_abs);
     auto ceil_f = [](double v) {
         float f = (float)v;
         if ((double)f < v) f = std::nextafter(f, INFINITY);
         return f;
     };
-    wa.lo_f = ceil_f(lo);
     wa.base_f = ceil_f(cfg->snr_min);
 
     SelArgs sa;

@@ -1,14 +1,18 @@
-// Algorithm 1 (Section 2.2.1, Eq. 3-4) on the GPU, one 1024-thread CTA per
-// folded profile, with the last FFA stage (Section 2.1) fused into the load.
+// Algorithm 1 (Section 2.2.1, Eq. 3-4) on the GPU, one CTA per folded
+// profile at a time (persistent over trials), with the last FFA stage
+// (Section 2.1) fused into the load.
 //
 // Layout.  The profile x (p0 bins) is extended cyclically to p0 + wmax bins
-// and cut into blocks of 32 consecutive bins; thread t owns block t in
-// registers.  Blocks beyond the first 1024 (long profiles) only take part in
-// the prefix step.
+// and cut into blocks of R consecutive bins; thread t owns block t in
+// registers.  Blocks beyond the first T (the cyclic extension) only take part
+// in the prefix step.  The CTA shape (T threads of R bins) follows the
+// profile length: 256 x 8 up to 2048 bins (several CTAs per SM), 512 x 16 up
+// to 8192, 1024 x 32 up to 32768 (one per SM), so that short profiles do not
+// leave most of a CTA idle.
 //
 // Median and MAD (exact).  A monotone bucket function (affine map of the
-// value, rounded, clamped) feeds a 2048-bin shared-memory histogram; the
-// bucket(s) holding the wanted ranks are gathered and sorted, which gives the
+// value, rounded, clamped) feeds a shared-memory histogram; the
+// bucket(s) holding the wanted ranks are gathered and ranked, which gives the
 // exact order statistics because a monotone bucket map preserves order
 // between buckets.  For float profiles the deviations |x - med| are bucketed
 // from their FP32 values |x - fl(med)|, which differ from the exact FP64
@@ -20,9 +24,9 @@
 //
 // Box sums.  With the in-block exclusive prefix c_t[o] (FP32) and the block
 // offsets Cb[t] = sum of earlier blocks (float-float), the cyclic box sum of
-// width w >= 32 starting at bin 32t + o is
-//     (Cb[t + w/32] - Cb[t]) + (c_{t+w/32}[o] - c_t[o]),
-// one shared-memory read, two adds and a max per bin; widths below 32 use the
+// width w >= R starting at bin Rt + o is
+//     (Cb[t + w/R] - Cb[t]) + (c_{t+w/R}[o] - c_t[o]),
+// one shared-memory read, two adds and a max per bin; widths below R use the
 // thread's own prefix and the next block's.  Int profiles use the same
 // formulas in wrapping int32 arithmetic, which is exact for box sums below
 // 2^31.  Only the maximum of each width is kept; the winning width's first
@@ -40,30 +44,50 @@ namespace ffa {
 
 namespace {
 
-constexpr int T2 = 1024;          // threads per CTA
-constexpr int R2 = 32;            // bins per block (per thread)
-constexpr int MAXB = 2048;        // max blocks incl. the cyclic extension (65536 bins)
-constexpr int NBK = 2048;         // histogram buckets
-constexpr int CAPM = 1024;        // gather capacity
+// CTA shapes.  A profile of p0 bins is cut into blocks of R bins, one per
+// thread; T * R >= p0.  Long profiles take 1024-thread CTAs, one per SM;
+// short ones smaller CTAs, several per SM, each on its own profile.
+template <int TH>
+struct Cfg;
+template <>
+struct Cfg<1024> {
+    static constexpr int T = 1024, R = 32, MAXB = 2048, NBK = 2048, CAPM = 1024, MINB = 1;
+};
+template <>
+struct Cfg<512> {
+    static constexpr int T = 512, R = 16, MAXB = 1024, NBK = 1024, CAPM = 512, MINB = 2;
+};
+template <>
+struct Cfg<256> {
+    static constexpr int T = 256, R = 8, MAXB = 512, NBK = 512, CAPM = 512, MINB = 4;
+};
+using CBig = Cfg<1024>;
 constexpr double KMAD = 1.4826;   // printed after Eq. 4
+
+#define FFA_CFG_ALIASES                                   \
+    constexpr int T2 = C::T, R2 = C::R, MAXB = C::MAXB;   \
+    constexpr int NBK = C::NBK, CAPM = C::CAPM;           \
+    constexpr int NW = T2 / 32;                           \
+    (void)T2; (void)R2; (void)MAXB; (void)NBK; (void)CAPM; (void)NW;
 
 // Shared-memory index of bin t: 4 pad words per 32-bin block keep every block
 // 16-byte aligned (vector loads) and spread blocked accesses over the banks.
 __device__ __forceinline__ int sidx(int t) { return t + 4 * (t >> 5); }
 
+template <class C>
 struct Sh2 {
-    uint32_t hist[NBK];
-    unsigned long long cand[CAPM];  // order-preserving keys of the candidates
-    float candf[CAPM];    // gathered values; FP64 is applied per candidate afterwards
-    double bw_max[16];    // per-width block maxima
-    float cbh[MAXB + 1];  // block offsets (hi) / int offsets reinterpreted
-    float cbl[MAXB + 1];  // block offsets (lo)
+    uint32_t hist[C::NBK];
+    unsigned long long cand[C::CAPM];  // order-preserving keys of the candidates
+    float candf[C::CAPM];    // gathered values; FP64 is applied per candidate afterwards
+    double bw_max[16];       // per-width block maxima
+    float cbh[C::MAXB + 1];  // block offsets (hi) / int offsets reinterpreted
+    float cbl[C::MAXB + 1];  // block offsets (lo)
     float wred[16][32];   // per-width warp maxima (float profiles)
     int wredi[16][32];    // per-width warp maxima (int profiles)
     float fred[32];
     double dred[64];
     int ired[32];
-    int ired2[CAPM];      // gathered int values
+    int ired2[C::CAPM];      // gathered int values
     unsigned long long ukey[2];
     uint32_t cnt, below;
     int bin_a, bin_b;
@@ -90,7 +114,9 @@ __device__ __forceinline__ int warp_mini(int v) {
 }
 
 // block sums of a and b and the max of c (one barrier pair)
-__device__ void blk_stats(float& a, float& b, float& c, Sh2& sh) {
+template <class C>
+__device__ void blk_stats(float& a, float& b, float& c, Sh2<C>& sh) {
+    FFA_CFG_ALIASES
     a = warp_sum(a);
     b = warp_sum(b);
     c = warp_max(c);
@@ -101,22 +127,27 @@ __device__ void blk_stats(float& a, float& b, float& c, Sh2& sh) {
         sh.wred[1][w] = c;
     }
     __syncthreads();
-    a = warp_sum(sh.fred[l]);
-    b = warp_sum(sh.wred[0][l]);
-    c = warp_max(sh.wred[1][l]);
+    a = warp_sum(l < NW ? sh.fred[l] : 0.0f);
+    b = warp_sum(l < NW ? sh.wred[0][l] : 0.0f);
+    c = warp_max(l < NW ? sh.wred[1][l] : 0.0f);
     __syncthreads();
 }
-__device__ int blk_mini(int v, Sh2& sh) {
+template <class C>
+__device__ int blk_mini(int v, Sh2<C>& sh) {
+    FFA_CFG_ALIASES
     v = warp_mini(v);
     if ((threadIdx.x & 31) == 0) sh.ired[threadIdx.x >> 5] = v;
     __syncthreads();
-    int r = warp_mini(sh.ired[threadIdx.x & 31]);
+    const int l = threadIdx.x & 31;
+    int r = warp_mini(l < NW ? sh.ired[l] : 0x7fffffff);
     __syncthreads();
     return r;
 }
 
 // exclusive scan of one uint32 per thread
-__device__ uint32_t blk_exscan_u(uint32_t v, Sh2& sh, uint32_t* total) {
+template <class C>
+__device__ uint32_t blk_exscan_u(uint32_t v, Sh2<C>& sh, uint32_t* total) {
+    FFA_CFG_ALIASES
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
     for (int o = 1; o < 32; o <<= 1) {
@@ -127,7 +158,7 @@ __device__ uint32_t blk_exscan_u(uint32_t v, Sh2& sh, uint32_t* total) {
     if (lane == 31) s[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        uint32_t y = s[lane];
+        uint32_t y = lane < NW ? s[lane] : 0u;
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t u = __shfl_up_sync(0xffffffffu, y, o);
             if (lane >= o) y += u;
@@ -136,7 +167,7 @@ __device__ uint32_t blk_exscan_u(uint32_t v, Sh2& sh, uint32_t* total) {
     }
     __syncthreads();
     uint32_t r = (warp ? s[warp - 1] : 0u) + x - v;
-    if (total) *total = s[31];
+    if (total) *total = s[NW - 1];
     __syncthreads();
     return r;
 }
@@ -156,7 +187,9 @@ __device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, f
     sh_ = s2;
 }
 
-__device__ void blk_exscan_ff(float vh, Sh2& sh, float& oh, float& ol, float& th, float& tl) {
+template <class C>
+__device__ void blk_exscan_ff(float vh, Sh2<C>& sh, float& oh, float& ol, float& th, float& tl) {
+    FFA_CFG_ALIASES
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float xh = vh, xl = 0.0f;
     for (int o = 1; o < 32; o <<= 1) {
@@ -171,7 +204,7 @@ __device__ void blk_exscan_ff(float vh, Sh2& sh, float& oh, float& ol, float& th
     }
     __syncthreads();
     if (warp == 0) {
-        float yh = sh.fred[lane], yl = sh.wred[0][lane];
+        float yh = lane < NW ? sh.fred[lane] : 0.0f, yl = lane < NW ? sh.wred[0][lane] : 0.0f;
         for (int o = 1; o < 32; o <<= 1) {
             float uh = __shfl_up_sync(0xffffffffu, yh, o);
             float ul = __shfl_up_sync(0xffffffffu, yl, o);
@@ -194,13 +227,15 @@ __device__ void blk_exscan_ff(float vh, Sh2& sh, float& oh, float& ol, float& th
     }
     oh = eh;
     ol = el;
-    th = sh.fred[31];
-    tl = sh.wred[0][31];
+    th = sh.fred[NW - 1];
+    tl = sh.wred[0][NW - 1];
     __syncthreads();
 }
 
 // ranks ra <= rb -> their bins and the counts below those bins, one scan
-__device__ void blk_find2(Sh2& sh, uint32_t ra, uint32_t rb) {
+template <class C>
+__device__ void blk_find2(Sh2<C>& sh, uint32_t ra, uint32_t rb) {
+    FFA_CFG_ALIASES
     const int per = NBK / T2;
     const int b0 = threadIdx.x * per;
     uint32_t s = 0;
@@ -223,7 +258,8 @@ __device__ void blk_find2(Sh2& sh, uint32_t ra, uint32_t rb) {
 }
 
 // single-rank variant (radix fallback)
-__device__ void blk_find(Sh2& sh, uint32_t rank, int* bin, uint32_t* below) {
+template <class C>
+__device__ void blk_find(Sh2<C>& sh, uint32_t rank, int* bin, uint32_t* below) {
     blk_find2(sh, rank, rank);
     *bin = sh.bin_a;
     *below = sh.below_a;
@@ -234,8 +270,10 @@ __device__ void blk_find(Sh2& sh, uint32_t rank, int* bin, uint32_t* below) {
 // the n x n integer comparisons are spread over the whole CTA and each
 // candidate's rank is accumulated in shared memory (sh.hist is free here).
 // Integer keys, not doubles: FP64 compares are slow on this part.
-__device__ void cand_pick2(Sh2& sh, uint32_t n, uint32_t ta, uint32_t tb, unsigned long long* ka,
+template <class C>
+__device__ void cand_pick2(Sh2<C>& sh, uint32_t n, uint32_t ta, uint32_t tb, unsigned long long* ka,
                            unsigned long long* kb) {
+    FFA_CFG_ALIASES
     for (uint32_t i = threadIdx.x; i < n; i += T2) sh.hist[i] = 0;
     __syncthreads();
     const uint32_t chunks = (T2 + n - 1) / (n ? n : 1);  // threads per candidate
@@ -265,8 +303,9 @@ __device__ void cand_pick2(Sh2& sh, uint32_t n, uint32_t ta, uint32_t tb, unsign
 // Exact rank-`rank` 64-bit key of keyf(j), j < n, by an 8-pass radix select
 // over the profile still held in shared memory (fallback when a gather
 // overflows; rare).
-template <class KeyF>
-__device__ __noinline__ uint64_t smem_select64(Sh2& sh, int n, uint32_t rank, KeyF keyf) {
+template <class C, class KeyF>
+__device__ __noinline__ uint64_t smem_select64(Sh2<C>& sh, int n, uint32_t rank, KeyF keyf) {
+    FFA_CFG_ALIASES
     uint64_t prefix = 0, mask = 0;
     for (int pass = 0; pass < 8; ++pass) {
         const int shift = 56 - 8 * pass;
@@ -298,12 +337,14 @@ struct Traits<int32_t> {
 };
 
 // bucket of a float value: rint((v - base) * inv + NBK/2) clamped, monotone in v
+template <int NBK>
 __device__ __forceinline__ int fbucket(float v, float base, float inv) {
     float f = __fmaf_rn(__fsub_rn(v, base), inv, (float)(NBK / 2));
     f = fminf(fmaxf(f, 0.0f), (float)(NBK - 1));
     return __float_as_int(__fadd_rn(f, 12582912.0f)) - 0x4B400000;
 }
 // int profiles (|x| < 2^28): floor((v - base) / 2^sh) + NBK/2, clamped; monotone
+template <int NBK>
 __device__ __forceinline__ int ibucket(int v, int base, int sh) {
     const int d = ((v - base) >> sh) + NBK / 2;  // arithmetic shift = floor division
     return d < 0 ? 0 : (d > NBK - 1 ? NBK - 1 : d);
@@ -317,7 +358,8 @@ template <class T>
 struct BoxOps;
 template <>
 struct BoxOps<float> {
-    static __device__ __forceinline__ float blockdiff(const Sh2& sh, int b2, int b1) {
+    template <class C>
+    static __device__ __forceinline__ float blockdiff(const Sh2<C>& sh, int b2, int b1) {
         return __fadd_rn(__fsub_rn(sh.cbh[b2], sh.cbh[b1]), __fsub_rn(sh.cbl[b2], sh.cbl[b1]));
     }
     static __device__ __forceinline__ float box(float D, float c2, float c1) {
@@ -328,7 +370,8 @@ struct BoxOps<float> {
 };
 template <>
 struct BoxOps<int32_t> {
-    static __device__ __forceinline__ int32_t blockdiff(const Sh2& sh, int b2, int b1) {
+    template <class C>
+    static __device__ __forceinline__ int32_t blockdiff(const Sh2<C>& sh, int b2, int b1) {
         const int* cbi = reinterpret_cast<const int*>(sh.cbh);
         return (int32_t)((uint32_t)cbi[b2] - (uint32_t)cbi[b1]);
     }
@@ -343,9 +386,10 @@ struct BoxOps<int32_t> {
 
 // Width W < 32 (compile time): own prefix, next block past the end.  With
 // FIND, returns the first position whose box equals `target` (else -1).
-template <class T, int W, bool FIND>
-__device__ __forceinline__ T small_width(const T (&c)[R2], const Sh2& sh, const T* buf, int tid,
+template <class T, int W, bool FIND, class C>
+__device__ __forceinline__ T small_width(const T (&c)[C::R], const Sh2<C>& sh, const T* buf, int tid,
                                          int nvalid, T target, int* first) {
+    FFA_CFG_ALIASES
     using B = BoxOps<T>;
     const T Town = B::blockdiff(sh, tid + 1, tid);
     constexpr int NC = W < 4 ? 4 : W;  // next block's first values, 128-bit loads
@@ -369,9 +413,10 @@ __device__ __forceinline__ T small_width(const T (&c)[R2], const Sh2& sh, const 
 }
 
 // Width w >= 32 (multiple of 32): block tid + w/32 at the same offsets.
-template <class T, bool FIND>
-__device__ __forceinline__ T wide_width(const T (&c)[R2], const Sh2& sh, const T* buf, int tid,
+template <class T, bool FIND, class C>
+__device__ __forceinline__ T wide_width(const T (&c)[C::R], const Sh2<C>& sh, const T* buf, int tid,
                                         int w, int nvalid, T target, int* first) {
+    FFA_CFG_ALIASES
     using B = BoxOps<T>;
     const int b2 = tid + w / R2;
     const T D = B::blockdiff(sh, b2, tid);
@@ -399,8 +444,10 @@ __device__ __forceinline__ void upk2(unsigned long long v, float& a, float& b) {
 
 // Wide widths, float profiles, maxima only: the same per-bin arithmetic as
 // wide_width (D + (c2 - c1), each rounded to nearest) on packed pairs.
-__device__ __forceinline__ float wide_width_f32x2(const float (&c)[R2], const Sh2& sh, const float* buf,
+template <class C>
+__device__ __forceinline__ float wide_width_f32x2(const float (&c)[C::R], const Sh2<C>& sh, const float* buf,
                                                   int tid, int w, int nvalid) {
+    FFA_CFG_ALIASES
     const int b2 = tid + w / R2;
     const float D = BoxOps<float>::blockdiff(sh, b2, tid);
     const unsigned long long DD = pk2(D, D);
@@ -425,31 +472,38 @@ __device__ __forceinline__ float wide_width_f32x2(const float (&c)[R2], const Sh
     return fmaxf(m, ma);
 }
 
-template <class T, bool FIND>
-__device__ __forceinline__ T width_max(const T (&c)[R2], const Sh2& sh, const T* buf, int tid, int w,
+template <class T, bool FIND, class C>
+__device__ __forceinline__ T width_max(const T (&c)[C::R], const Sh2<C>& sh, const T* buf, int tid, int w,
                                        int nvalid, T target, int* first) {
-    switch (w) {
-        case 1: return small_width<T, 1, FIND>(c, sh, buf, tid, nvalid, target, first);
-        case 2: return small_width<T, 2, FIND>(c, sh, buf, tid, nvalid, target, first);
-        case 4: return small_width<T, 4, FIND>(c, sh, buf, tid, nvalid, target, first);
-        case 8: return small_width<T, 8, FIND>(c, sh, buf, tid, nvalid, target, first);
-        case 16: return small_width<T, 16, FIND>(c, sh, buf, tid, nvalid, target, first);
-        default:
-            if constexpr (!FIND && !Traits<T>::is_int) return wide_width_f32x2(c, sh, buf, tid, w, nvalid);
-            else return wide_width<T, FIND>(c, sh, buf, tid, w, nvalid, target, first);
+    if (w < C::R) {
+        switch (w) {
+            case 1: return small_width<T, 1, FIND>(c, sh, buf, tid, nvalid, target, first);
+            case 2: return small_width<T, 2, FIND>(c, sh, buf, tid, nvalid, target, first);
+            case 4: return small_width<T, 4, FIND>(c, sh, buf, tid, nvalid, target, first);
+            case 8:
+                if constexpr (8 < C::R) return small_width<T, 8, FIND>(c, sh, buf, tid, nvalid, target, first);
+                break;
+            case 16:
+                if constexpr (16 < C::R) return small_width<T, 16, FIND>(c, sh, buf, tid, nvalid, target, first);
+                break;
+            default: break;
+        }
     }
+    if constexpr (!FIND && !Traits<T>::is_int) return wide_width_f32x2(c, sh, buf, tid, w, nvalid);
+    else return wide_width<T, FIND>(c, sh, buf, tid, w, nvalid, target, first);
 }
 
 // prof: FUSED ? the stage-(m-1) plane (m_rows rows of p0) : profiles of p0.
 // Record i belongs to trial trial0 + i, i < count.
-template <class T, bool FUSED>
-__global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, int64_t p0_,
-                                                  int64_t m_rows, int64_t trial0, int64_t count,
-                                                  ScoreWidths wd, ffa_record* __restrict__ rec,
-                                                  int32_t* d_status) {
+template <class C, class T, bool FUSED>
+__global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ prof, int64_t p0_,
+                                                          int64_t m_rows, int64_t trial0, int64_t count,
+                                                          ScoreWidths wd, ffa_record* __restrict__ rec,
+                                                          int32_t* d_status) {
+    FFA_CFG_ALIASES
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Sh2& sh = *reinterpret_cast<Sh2*>(smem_raw);
-    T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(Sh2) + 15) & ~(size_t)15));
+    Sh2<C>& sh = *reinterpret_cast<Sh2<C>*>(smem_raw);
+    T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(Sh2<C>) + 15) & ~(size_t)15));
     using B = BoxOps<T>;
     const int p0 = (int)p0_;
     const int tid = threadIdx.x;
@@ -550,8 +604,8 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
         while ((double)(1ll << ish) < span && ish < 40) ++ish;
     }
     auto bucket_m = [&](T v) -> int {
-        if constexpr (Traits<T>::is_int) return ibucket((int)v, ibase, ish);
-        else return fbucket((float)v, mean, inv_m);
+        if constexpr (Traits<T>::is_int) return ibucket<NBK>((int)v, ibase, ish);
+        else return fbucket<NBK>((float)v, mean, inv_m);
     };
     if (nvalid > 0) {
 #pragma unroll
@@ -812,12 +866,12 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
         }
     }
     __syncthreads();
-    // per-width block maxima: warp w reduces width w's 32 warp maxima
-    if (warp < wd.n) {
+    // per-width block maxima: warp w reduces the warp maxima of widths w, w + NW, ...
+    for (int wi = warp; wi < wd.n; wi += NW) {
         double Bw;
-        if constexpr (Traits<T>::is_int) Bw = (double)warp_maxi(sh.wredi[warp][lane]);
-        else Bw = (double)warp_max(sh.wred[warp][lane]);
-        if (lane == 0) sh.bw_max[warp] = Bw;
+        if constexpr (Traits<T>::is_int) Bw = (double)warp_maxi(lane < NW ? sh.wredi[wi][lane] : INT32_MIN);
+        else Bw = (double)warp_max(lane < NW ? sh.wred[wi][lane] : -INFINITY);
+        if (lane == 0) sh.bw_max[wi] = Bw;
     }
     __syncthreads();
     // S/N_w = (B_w - w*med) / (K*MAD*sqrt(w)) in FP64.  Widths are ranked with
@@ -859,8 +913,8 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
     __syncthreads();
     // first argmax of the winning width, recomputed bit-identically
     T target;
-    if constexpr (Traits<T>::is_int) target = (T)warp_maxi(sh.wredi[bw][lane]);
-    else target = (T)warp_max(sh.wred[bw][lane]);
+    if constexpr (Traits<T>::is_int) target = (T)warp_maxi(lane < NW ? sh.wredi[bw][lane] : INT32_MIN);
+    else target = (T)warp_max(lane < NW ? sh.wred[bw][lane] : -INFINITY);
     int first = -1;
     if (own && mad > 0.0) (void)width_max<T, true>(x, sh, buf, tid, wd.w[bw], nvalid, target, &first);
     const int pos = blk_mini(first >= 0 ? base_pos + first : 0x7fffffff, sh);
@@ -892,8 +946,9 @@ __global__ void __launch_bounds__(T2, 1) k_score2(const T* __restrict__ prof, in
 // Sums are taken about w * mean(x) (the mean of every filtered profile) so
 // that the FP32 sums of squares do not cancel; I_av and sigma in FP64.
 // ---------------------------------------------------------------------------
-template <class T>
-__device__ __forceinline__ T box_at(const T (&c)[R2], const Sh2& sh, const T* buf, int tid, int w, int r) {
+template <class T, class C>
+__device__ __forceinline__ T box_at(const T (&c)[C::R], const Sh2<C>& sh, const T* buf, int tid, int w, int r) {
+    FFA_CFG_ALIASES
     using B = BoxOps<T>;
     // cyclic box of width w starting at bin 32 tid + r, from the blocked prefix
     const int j2 = tid * R2 + r + w;
@@ -901,14 +956,15 @@ __device__ __forceinline__ T box_at(const T (&c)[R2], const Sh2& sh, const T* bu
     return B::box(B::blockdiff(sh, b2, tid), buf[sidx(b2 * R2 + o2)], c[r]);
 }
 
-template <class T, bool FUSED>
-__global__ void __launch_bounds__(T2, 1) k_score_alg2(const T* __restrict__ prof, int64_t p0_,
-                                                      int64_t m_rows, int64_t trial0, int64_t count,
-                                                      ScoreWidths wd, float excl_frac,
-                                                      ffa_record* __restrict__ rec) {
+template <class C, class T, bool FUSED>
+__global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restrict__ prof, int64_t p0_,
+                                                              int64_t m_rows, int64_t trial0, int64_t count,
+                                                              ScoreWidths wd, float excl_frac,
+                                                              ffa_record* __restrict__ rec) {
+    FFA_CFG_ALIASES
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Sh2& sh = *reinterpret_cast<Sh2*>(smem_raw);
-    T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(Sh2) + 15) & ~(size_t)15));
+    Sh2<C>& sh = *reinterpret_cast<Sh2<C>*>(smem_raw);
+    T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(Sh2<C>) + 15) & ~(size_t)15));
     using B = BoxOps<T>;
     const int p0 = (int)p0_;
     const int tid = threadIdx.x;
@@ -1049,10 +1105,10 @@ __global__ void __launch_bounds__(T2, 1) k_score_alg2(const T* __restrict__ prof
                 sh.wred[2][warp] = s2;
             }
             __syncthreads();
-            mf = sh.wred[0][lane];
-            mpos = sh.wredi[0][lane];
-            s1 = sh.wred[1][lane];
-            s2 = sh.wred[2][lane];
+            mf = lane < NW ? sh.wred[0][lane] : -INFINITY;
+            mpos = lane < NW ? sh.wredi[0][lane] : 0x7fffffff;
+            s1 = lane < NW ? sh.wred[1][lane] : 0.0f;
+            s2 = lane < NW ? sh.wred[2][lane] : 0.0f;
             for (int o = 16; o > 0; o >>= 1) {
                 const float om = __shfl_xor_sync(0xffffffffu, mf, o);
                 const int op = __shfl_xor_sync(0xffffffffu, mpos, o);
@@ -1091,8 +1147,8 @@ __global__ void __launch_bounds__(T2, 1) k_score_alg2(const T* __restrict__ prof
                 sh.wred[4][warp] = w2;
             }
             __syncthreads();
-            w1 = sh.wred[3][lane];
-            w2 = sh.wred[4][lane];
+            w1 = lane < NW ? sh.wred[3][lane] : 0.0f;
+            w2 = lane < NW ? sh.wred[4][lane] : 0.0f;
             for (int o = 16; o > 0; o >>= 1) {
                 w1 += __shfl_xor_sync(0xffffffffu, w1, o);
                 w2 += __shfl_xor_sync(0xffffffffu, w2, o);
@@ -1133,70 +1189,119 @@ __global__ void __launch_bounds__(T2, 1) k_score_alg2(const T* __restrict__ prof
     }
 }
 
+namespace {
+
+template <class C>
 size_t score2_smem_bytes(int64_t p0, int wmax, size_t elem) {
-    int64_t nbe = (p0 + wmax + R2) / R2 + 1;
-    int64_t nbins = (nbe > T2 ? nbe : T2) * R2 + R2;
-    return ((sizeof(Sh2) + 15) & ~(size_t)15) + (size_t)(nbins + 4 * (nbins / 32) + 64) * elem;
+    const int64_t nbe = (p0 + wmax + C::R) / C::R + 1;
+    const int64_t nbins = (nbe > C::T ? nbe : C::T) * C::R + C::R;
+    return ((sizeof(Sh2<C>) + 15) & ~(size_t)15) + (size_t)(nbins + 4 * (nbins / 32) + 64) * elem;
 }
+
+// does a profile of p0 bins with widths up to wmax fit configuration C?
+template <class C>
+bool fits(int64_t p0, int wmax) {
+    return p0 >= 1 && (p0 + C::R - 1) / C::R <= C::T && (p0 + wmax + C::R) / C::R + 1 <= C::MAXB;
+}
+
+template <class C, class TT, bool FF>
+ffa_status launch_score2_cfg(const void* d_prof, int64_t count, int64_t trial0, int64_t p0, int64_t m_rows,
+                             const ScoreWidths& wd, ffa_record* d_rec, int32_t* d_status, cudaStream_t st) {
+    const int wmax = wd.w[wd.n - 1];
+    const size_t smem = score2_smem_bytes<C>(p0, wmax, 4);
+    if (smem > 227 * 1024) return fail(FFA_ERR_UNSUPPORTED, "score: profile too long for shared memory");
+    const void* fn = (const void*)k_score2<C, TT, FF>;
+    ffa_status es = ensure_smem(fn, smem);
+    if (es != FFA_OK) return es;
+    int dev = 0, nsm = 0, per_sm = 0;
+    FFA_CUDA_TRY(cudaGetDevice(&dev));
+    FFA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    FFA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, C::T, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t resident = (int64_t)nsm * per_sm;  // persistent: every CTA resident
+    const unsigned grid = (unsigned)(count < resident ? count : resident);
+    k_score2<C, TT, FF><<<grid, C::T, smem, st>>>((const TT*)d_prof, p0, m_rows, trial0, count, wd, d_rec,
+                                                  d_status);
+    FFA_LAUNCH_CHECK("k_score2");
+    count_launch();
+    return FFA_OK;
+}
+
+template <class TT, bool FF>
+ffa_status launch_score2_t(const void* d_prof, int64_t count, int64_t trial0, int64_t p0, int64_t m_rows,
+                           const ScoreWidths& wd, ffa_record* d_rec, int32_t* d_status, cudaStream_t st) {
+    const int wmax = wd.w[wd.n - 1];
+    if (fits<Cfg<256>>(p0, wmax))
+        return launch_score2_cfg<Cfg<256>, TT, FF>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
+    if (fits<Cfg<512>>(p0, wmax))
+        return launch_score2_cfg<Cfg<512>, TT, FF>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
+    return launch_score2_cfg<CBig, TT, FF>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
+}
+
+}  // namespace
 
 ffa_status launch_score2(const void* d_prof, int32_t precision, bool fused, int64_t count,
                          int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
                          ffa_record* d_rec, int32_t* d_status, cudaStream_t st) {
     if (count <= 0) return FFA_OK;
     const int wmax = wd.w[wd.n - 1];
-    if (p0 < 1 || (p0 + wmax + R2) / R2 + 1 > MAXB || (p0 + R2 - 1) / R2 > T2)
-        return fail(FFA_ERR_UNSUPPORTED, "score: profile longer than 32768 bins");
-    size_t smem = score2_smem_bytes(p0, wmax, 4);
+    if (!fits<CBig>(p0, wmax)) return fail(FFA_ERR_UNSUPPORTED, "score: profile longer than 32768 bins");
+    if (precision == FFA_FOLD_F32)
+        return fused ? launch_score2_t<float, true>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st)
+                     : launch_score2_t<float, false>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
+    return fused ? launch_score2_t<int32_t, true>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st)
+                 : launch_score2_t<int32_t, false>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
+}
+
+namespace {
+
+template <class C, class TT, bool FF>
+ffa_status launch_alg2_cfg(const void* d_prof, int64_t count, int64_t trial0, int64_t p0, int64_t m_rows,
+                           const ScoreWidths& wd, float excl_frac, ffa_record* d_rec, cudaStream_t st) {
+    const int wmax = wd.w[wd.n - 1];
+    const size_t smem = score2_smem_bytes<C>(p0, wmax, 4);
     if (smem > 227 * 1024) return fail(FFA_ERR_UNSUPPORTED, "score: profile too long for shared memory");
-    int dev = 0, nsm = 0;
+    const void* fn = (const void*)k_score_alg2<C, TT, FF>;
+    ffa_status es = ensure_smem(fn, smem);
+    if (es != FFA_OK) return es;
+    int dev = 0, nsm = 0, per_sm = 0;
     FFA_CUDA_TRY(cudaGetDevice(&dev));
     FFA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const unsigned grid = (unsigned)(count < nsm ? count : nsm);  // one resident CTA per SM
-    ffa_status es;
-#define FFA_S2(TT, FF)                                                                       \
-    es = ensure_smem((const void*)k_score2<TT, FF>, smem);                                   \
-    if (es != FFA_OK) return es;                                                             \
-    k_score2<TT, FF><<<grid, T2, smem, st>>>((const TT*)d_prof, p0, m_rows, trial0, count, wd, \
-                                             d_rec, d_status);
-    if (precision == FFA_FOLD_F32) {
-        if (fused) { FFA_S2(float, true) } else { FFA_S2(float, false) }
-    } else {
-        if (fused) { FFA_S2(int32_t, true) } else { FFA_S2(int32_t, false) }
-    }
-#undef FFA_S2
-    FFA_LAUNCH_CHECK("k_score2");
+    FFA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, C::T, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t resident = (int64_t)nsm * per_sm;
+    const unsigned grid = (unsigned)(count < resident ? count : resident);
+    k_score_alg2<C, TT, FF><<<grid, C::T, smem, st>>>((const TT*)d_prof, p0, m_rows, trial0, count, wd,
+                                                      excl_frac, d_rec);
+    FFA_LAUNCH_CHECK("k_score_alg2");
     count_launch();
     return FFA_OK;
 }
+
+template <class TT, bool FF>
+ffa_status launch_alg2_t(const void* d_prof, int64_t count, int64_t trial0, int64_t p0, int64_t m_rows,
+                         const ScoreWidths& wd, float excl_frac, ffa_record* d_rec, cudaStream_t st) {
+    const int wmax = wd.w[wd.n - 1];
+    if (fits<Cfg<256>>(p0, wmax))
+        return launch_alg2_cfg<Cfg<256>, TT, FF>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
+    if (fits<Cfg<512>>(p0, wmax))
+        return launch_alg2_cfg<Cfg<512>, TT, FF>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
+    return launch_alg2_cfg<CBig, TT, FF>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
+}
+
+}  // namespace
 
 ffa_status launch_score_alg2(const void* d_prof, int32_t precision, bool fused, int64_t count,
                              int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
                              float excl_frac, ffa_record* d_rec, cudaStream_t st) {
     if (count <= 0) return FFA_OK;
     const int wmax = wd.w[wd.n - 1];
-    if (p0 < 1 || (p0 + wmax + R2) / R2 + 1 > MAXB || (p0 + R2 - 1) / R2 > T2)
-        return fail(FFA_ERR_UNSUPPORTED, "score: profile longer than 32768 bins");
-    const size_t smem = score2_smem_bytes(p0, wmax, 4);
-    if (smem > 227 * 1024) return fail(FFA_ERR_UNSUPPORTED, "score: profile too long for shared memory");
-    int dev = 0, nsm = 0;
-    FFA_CUDA_TRY(cudaGetDevice(&dev));
-    FFA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const unsigned grid = (unsigned)(count < nsm ? count : nsm);
-    ffa_status es;
-#define FFA_A2(TT, FF)                                                                          \
-    es = ensure_smem((const void*)k_score_alg2<TT, FF>, smem);                                  \
-    if (es != FFA_OK) return es;                                                                \
-    k_score_alg2<TT, FF><<<grid, T2, smem, st>>>((const TT*)d_prof, p0, m_rows, trial0, count, wd, \
-                                                 excl_frac, d_rec);
-    if (precision == FFA_FOLD_F32) {
-        if (fused) { FFA_A2(float, true) } else { FFA_A2(float, false) }
-    } else {
-        if (fused) { FFA_A2(int32_t, true) } else { FFA_A2(int32_t, false) }
-    }
-#undef FFA_A2
-    FFA_LAUNCH_CHECK("k_score_alg2");
-    count_launch();
-    return FFA_OK;
+    if (!fits<CBig>(p0, wmax)) return fail(FFA_ERR_UNSUPPORTED, "score: profile longer than 32768 bins");
+    if (precision == FFA_FOLD_F32)
+        return fused ? launch_alg2_t<float, true>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st)
+                     : launch_alg2_t<float, false>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
+    return fused ? launch_alg2_t<int32_t, true>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st)
+                 : launch_alg2_t<int32_t, false>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
 }
 
 }  // namespace ffa

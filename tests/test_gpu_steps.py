@@ -186,6 +186,9 @@ def _check_records(got, ref, profiles, tol):
 @pytest.mark.parametrize("p0,widths", [(1, (1,)), (2, (1, 2)), (9, (1, 2, 4)), (256, (1, 2, 4, 8, 16)),
                                        (511, (1, 2, 4, 8, 16, 32, 64, 128)),
                                        (1953, tuple(2 ** i for i in range(10))),
+                                       (2048, tuple(2 ** i for i in range(12))),
+                                       (4093, tuple(2 ** i for i in range(11))),
+                                       (8192, tuple(2 ** i for i in range(12))),
                                        (15625, tuple(2 ** i for i in range(12))),
                                        (31249, tuple(2 ** i for i in range(13))),
                                        (32768, tuple(2 ** i for i in range(14)))])
@@ -205,6 +208,7 @@ def test_score_float(F, orc, dev, p0, widths):
 
 @pytest.mark.parametrize("p0,widths", [(5, (1, 2, 4)), (256, (1, 2, 4, 8, 16)),
                                        (1953, tuple(2 ** i for i in range(10))),
+                                       (6000, tuple(2 ** i for i in range(11))),
                                        (15625, tuple(2 ** i for i in range(12)))])
 def test_score_int_bit_exact(F, orc, dev, p0, widths):
     rng = np.random.default_rng(p0 + 1)
