@@ -298,7 +298,9 @@ def run_gpu(args):
     def step():
         ffa.search(plan, xs, workspace=ws, records=rec, status=status, stream=stream)
 
-    # warm-up (also surfaces device-side check failures before timing)
+    # fold pass depths tuned for this plan's shapes (untimed), then warm-up
+    # (which also surfaces device-side check failures before timing)
+    n_tuned = ffa.autotune(plan, ws, stream=stream)
     for _ in range(args.warmup):
         step()
     ffa.wait(status, stream=stream)
@@ -385,6 +387,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(desc, l2="inputs and fold planes larger than L2 (no flush needed)",
                            trials=int(plan.n_trials), base_periods=int(plan.n_periods),
+                           autotuned_fold_shapes=int(n_tuned),
                            samples_x_trials=units),
             "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": alu_achieved / alu_peak, "traffic": traffic,

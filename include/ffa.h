@@ -173,6 +173,15 @@ ffa_status ffa_search_persistence(const ffa_plan* plan, const void* d_series, vo
                                   size_t workspace_bytes, ffa_record* d_records, uint32_t* d_persist,
                                   int32_t* d_status, void* stream);
 
+/* Autotuner: for every fold shape of the plan (stage count, floor(log2 P0)),
+ * time the FFA with at most 3, 4 and 5 stages per HBM pass on its median
+ * base period and keep the fastest for every later search on this device
+ * (process-wide cache).  The pass depth never changes a result: every split
+ * runs the recursion's add tree.  Uses the workspace as scratch; blocks until
+ * the timing launches on `stream` finish.  *n_tuned = shapes tuned. */
+ffa_status ffa_autotune(const ffa_plan* plan, void* d_workspace, size_t workspace_bytes, void* stream,
+                        int32_t* n_tuned);
+
 /* A batch of series (e.g. dedispersion trials of uneven length), each with
  * its own plan: series i is searched with plans[i] into d_records[i] (host
  * arrays of `count` pointers).  One workspace, at least the largest plan's

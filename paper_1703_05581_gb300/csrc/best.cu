@@ -10,7 +10,9 @@
 //      resumes every chunk's speculative walk from that point in parallel.
 //      Two walks meet at the first record that raises or ends both of their
 //      candidates, so the sequential part is short.  Every peak is reported
-//      once, by the phase that processes the record ending its candidate.
+//      once, by the phase that processes the record ending its candidate;
+//      the sequential phase's peaks are kept (k_best_refix replays them in
+//      the later passes instead of walking again).
 //      The first pass (phases B and C) stores up to PEAK_CAP peak keys and
 //      counts every peak by its top 16 key bits.  With more peaks than that,
 //      k_best_plan narrows a radix select of the SEL_MAX-th strongest key 16
@@ -49,6 +51,7 @@ constexpr int WALK_CHUNK = 16384;   // records per warp chunk (a multiple of 32)
 constexpr int SEL_THREADS = 1024;
 
 constexpr int HIST_BINS = 1 << 16;
+constexpr int FIX_CAP = 1 << 20;    // peaks of the sequential phase kept for the later passes
 
 struct BestCtl {
     uint32_t n_peaks;   // peaks in the periodogram (counted by the first walk)
@@ -61,7 +64,7 @@ struct BestCtl {
     int32_t shift;      // next walk: histogram bits [shift, shift + 16)
     uint32_t need;      // keys still wanted within the prefix group
     uint32_t taken;     // keys known to be stronger than the prefix group
-    uint32_t pad;
+    uint32_t n_fix;     // peaks the first sequential pass reported
     unsigned long long prefix, mask, thr;
 };
 
@@ -92,7 +95,7 @@ struct SelArgs {
 };
 
 struct Layout {
-    size_t hist, peaks, ent, fr, out, ck, end_state, merge, total;
+    size_t hist, peaks, ent, fr, out, ck, end_state, merge, fix, total;
 };
 
 Layout layout(int64_t n_entries, int64_t n_trials) {
@@ -116,6 +119,8 @@ Layout layout(int64_t n_entries, int64_t n_trials) {
     off = al(off + sizeof(unsigned long long) * std::max<size_t>(n_chunks, 1));
     L.merge = off;
     off = al(off + sizeof(int32_t) * std::max<size_t>(n_chunks, 1));
+    L.fix = off;
+    off = al(off + sizeof(unsigned long long) * FIX_CAP);
     L.total = off;
     return L;
 }
@@ -137,6 +142,7 @@ __global__ void k_best_init(BestCtl* ctl, uint32_t* hist) {
         ctl->shift = 48;
         ctl->need = SEL_MAX;
         ctl->taken = 0;
+        ctl->n_fix = 0;
         ctl->prefix = 0;
         ctl->mask = 0;
         ctl->thr = 0;
@@ -150,12 +156,17 @@ struct WalkMode {
     int emit;    // store keys <= thr
     int shift;   // otherwise: histogram bits [shift, shift + 16) of keys in the prefix group
     unsigned long long prefix, mask, thr;
+    unsigned long long* fixlist;  // non-null: also keep the key for the later passes
 };
 
 __device__ __forceinline__ void emit_peak(BestCtl* ctl, unsigned long long* peaks, uint32_t* hist,
                                           const WalkMode& md, float pk, int64_t pi, int lane) {
     if (lane != 0) return;
     const unsigned long long key = peak_key(pk, pi);
+    if (md.fixlist) {
+        const uint32_t f = atomicAdd(&ctl->n_fix, 1u);
+        if (f < (uint32_t)FIX_CAP) md.fixlist[f] = key;
+    }
     if (md.first) {
         atomicAdd(&ctl->n_peaks, 1u);
         atomicAdd(&hist[key >> 48], 1u);
@@ -299,6 +310,7 @@ __device__ __forceinline__ WalkMode load_mode(int first, const BestCtl* ctl) {
     md.emit = 0;
     md.shift = 48;
     md.prefix = md.mask = md.thr = 0;
+    md.fixlist = nullptr;
     if (!first) {
         md.emit = ctl->emit;
         md.shift = ctl->shift;
@@ -343,9 +355,13 @@ __global__ void __launch_bounds__(32) k_best_fix(const ffa_record* __restrict__ 
                                                  int first, const unsigned long long* __restrict__ ck,
                                                  const unsigned long long* __restrict__ end_state,
                                                  int32_t* __restrict__ merge, BestCtl* ctl,
-                                                 unsigned long long* peaks, uint32_t* hist) {
-    if (!first && ctl->done) return;
-    const WalkMode md = load_mode(first, ctl);
+                                                 unsigned long long* peaks, uint32_t* hist,
+                                                 unsigned long long* fixlist) {
+    // later passes replay the first pass's peaks from fixlist (k_best_refix)
+    // unless there were too many to keep
+    if (!first && (ctl->done || ctl->n_fix <= (uint32_t)FIX_CAP)) return;
+    WalkMode md = load_mode(first, ctl);
+    if (first) md.fixlist = fixlist;
     const int lane = threadIdx.x & 31;
     const int64_t n_chunks = (n + WALK_CHUNK - 1) / WALK_CHUNK;
     WalkState w = decode(OUTSIDE, a);
@@ -369,6 +385,20 @@ __global__ void __launch_bounds__(32) k_best_fix(const ffa_record* __restrict__ 
         if (t < nb) w = decode(end_state[c], a);
     }
     if (w.inside) emit_peak(ctl, peaks, hist, md, w.pk, w.pi, lane);
+}
+
+// Phase B of a later pass, replayed: the first pass's sequential-phase peaks,
+// reported again in the current pass's mode.
+__global__ void __launch_bounds__(256) k_best_refix(BestCtl* ctl, const unsigned long long* __restrict__ fixlist,
+                                                    unsigned long long* peaks, uint32_t* hist) {
+    if (ctl->done || ctl->n_fix > (uint32_t)FIX_CAP) return;
+    const WalkMode md = load_mode(0, ctl);
+    const uint32_t nf = ctl->n_fix;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
+        const unsigned long long key = fixlist[i];
+        emit_peak(ctl, peaks, hist, md, fkey_inv(0xffffffffu - (uint32_t)(key >> 32)),
+                  (int64_t)(uint32_t)(key & 0xffffffffull), 0);
+    }
 }
 
 // Phase C (parallel, per radix level): each chunk's speculative walk resumed
@@ -639,6 +669,7 @@ extern "C" ffa_status ffa2best(const ffa_plan* p, const ffa_record* d_records,
     unsigned long long* ck = (unsigned long long*)(base + L.ck);
     unsigned long long* end_state = (unsigned long long*)(base + L.end_state);
     int32_t* merge = (int32_t*)(base + L.merge);
+    unsigned long long* fixlist = (unsigned long long*)(base + L.fix);
 
     // host tables: base periods, and the prime fractions sorted by value
     std::vector<BestEntry> he((size_t)n_ent);
@@ -694,16 +725,17 @@ extern "C" ffa_status ffa2best(const ffa_plan* p, const ffa_record* d_records,
     const int64_t nt = p->n_trials;
     k_best_init<<<64, 1024, 0, st>>>(ctl, hist);
     k_best_spec<<<152 * 8, 256, 0, st>>>(d_records, nt, wa, ck, end_state);
-    k_best_fix<<<1, 32, 0, st>>>(d_records, nt, wa, 1, ck, end_state, merge, ctl, peaks, hist);
+    k_best_fix<<<1, 32, 0, st>>>(d_records, nt, wa, 1, ck, end_state, merge, ctl, peaks, hist, fixlist);
     k_best_tail<<<152 * 8, 256, 0, st>>>(d_records, nt, wa, 1, ck, merge, ctl, peaks, hist);
     for (int level = 0; level < 4; ++level) {  // narrowing passes; no-ops once done
         k_best_plan<<<1, 1024, 0, st>>>(ctl, hist);
-        k_best_fix<<<1, 32, 0, st>>>(d_records, nt, wa, 0, ck, end_state, merge, ctl, peaks, hist);
+        k_best_refix<<<152, 256, 0, st>>>(ctl, fixlist, peaks, hist);
+        k_best_fix<<<1, 32, 0, st>>>(d_records, nt, wa, 0, ck, end_state, merge, ctl, peaks, hist, fixlist);
         k_best_tail<<<152 * 8, 256, 0, st>>>(d_records, nt, wa, 0, ck, merge, ctl, peaks, hist);
     }
     k_best_select<<<1, SEL_THREADS, smem, st>>>(d_records, ent, fr_g, fr_c, peaks, ctl, sa, dout);
     FFA_LAUNCH_CHECK("ffa2best kernels");
-    count_launch(16);
+    count_launch(20);
     ffa_status s = ffa_wait(stream, d_status, timeout_ms);
     if (s != FFA_OK) return s;
     BestCtl h;

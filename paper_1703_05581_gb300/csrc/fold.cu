@@ -21,7 +21,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 #include "internal.h"
@@ -36,9 +38,25 @@ struct FoldIn<float> { using type = float; };
 template <>
 struct FoldIn<int32_t> { using type = int8_t; };
 
+// Asynchronous 4-byte global -> shared copy (cp.async): a lane issues all of
+// its copies for a tile without waiting, then waits once (cp_async_wait).
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <class T, class S>
+__device__ __forceinline__ void put_async(T* dst, const S* src) {
+    if constexpr (sizeof(T) == sizeof(S)) cp_async4(dst, src);
+    else *dst = (T)*src;  // int8 series into int32 rows: converted through registers
+}
+
 // Stage `wt` cyclic columns of a row starting at column `base` (< p0) into
 // shared memory: at most one wrap when wt <= p0, so the segment is two
-// contiguous runs; loads are unrolled so that several are in flight per lane.
+// contiguous runs.  Same-width rows are copied with cp.async (the caller
+// waits with cp_async_wait before its barrier), so every row of a tile is in
+// flight at once.
 template <class T, class S>
 __device__ __forceinline__ void stage_row(T* __restrict__ rowp, const S* __restrict__ src, int64_t base,
                                           int64_t p0, int wt, bool live, int lane) {
@@ -50,14 +68,14 @@ __device__ __forceinline__ void stage_row(T* __restrict__ rowp, const S* __restr
         const int n1 = (int)((p0 - base) < wt ? (p0 - base) : wt);  // columns before the wrap
         const S* a = src + base;
 #pragma unroll 4
-        for (int x = lane; x < n1; x += 32) rowp[x] = (T)a[x];
+        for (int x = lane; x < n1; x += 32) put_async(rowp + x, a + x);
 #pragma unroll 4
-        for (int x = n1 + lane; x < wt; x += 32) rowp[x] = (T)src[x - n1];
+        for (int x = n1 + lane; x < wt; x += 32) put_async(rowp + x, src + (x - n1));
     } else {
         int64_t col = base + lane;
         while (col >= p0) col -= p0;
         for (int x = lane; x < wt; x += 32) {
-            rowp[x] = (T)src[col];
+            put_async(rowp + x, src + col);
             col += 32;
             while (col >= p0) col -= p0;
         }
@@ -103,6 +121,7 @@ __global__ void __launch_bounds__(FP_THREADS) k_fold_pass(const void* __restrict
         else
             stage_row(buf0 + u * wt, (const T*)src_v + ((g << s) + kappa) * p0, base, p0, wt, true, lane);
     }
+    cp_async_wait();
     __syncthreads();
     T* in = buf0;
     T* out = buf1;
@@ -225,6 +244,7 @@ __global__ void __launch_bounds__(F4_THREADS, 2) k_fold_reg(const void* __restri
         else
             stage_row(bufA + u * WA, (const T*)src_v + ((g << s) + kappa) * p0, base, p0, WT, true, lane);
     }
+    cp_async_wait();
     __syncthreads();
     const int64_t grow0 = (blk << (s + q)) + (kappa << q);
     const int64_t ncols = (c + F4_B <= p0) ? F4_B : p0 - c;
@@ -330,8 +350,7 @@ static ffa_status pass_q(int q, const void* src, T* dst, int64_t p0, int64_t m_r
 
 template <class T>
 static ffa_status fold_impl(const void* d_z, int64_t p0, int64_t m_data, int64_t m_rows,
-                            int stages, T* d_plane, T* d_tmp, cudaStream_t st) {
-    const int qmax = 5;
+                            int stages, T* d_plane, T* d_tmp, cudaStream_t st, int qmax) {
     int qs[64];
     int np = split_passes(stages, qmax, qs);
     if (np == 0) {
@@ -353,6 +372,79 @@ static ffa_status fold_impl(const void* d_z, int64_t p0, int64_t m_data, int64_t
     return FFA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Stages per pass, tuned.  Any split of the stages into passes gives the
+// same add tree (bit-identical planes); only the time differs.  The cache
+// maps (device, precision, stages, floor(log2 p0)) to the fastest maximum
+// pass depth measured by tune_fold; untuned shapes use 5.
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune;
+constexpr int QMAX_DEFAULT = 5;
+
+int log2i(int64_t v) {
+    int r = 0;
+    while ((int64_t)2 << r <= v) ++r;
+    return r;
+}
+
+int tuned_qmax(int precision, int stages, int64_t p0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QMAX_DEFAULT;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(dev, precision, stages, log2i(p0)));
+    return it == g_tune.end() ? QMAX_DEFAULT : it->second;
+}
+}  // namespace
+
+ffa_status fold_with(const void* d_z, int32_t precision, int64_t p0, int64_t m_data, int64_t m_rows,
+                     int stages, void* d_plane, void* d_tmp, cudaStream_t st, int qmax) {
+    if (precision == FFA_FOLD_F32)
+        return fold_impl<float>(d_z, p0, m_data, m_rows, stages, (float*)d_plane, (float*)d_tmp, st, qmax);
+    return fold_impl<int32_t>(d_z, p0, m_data, m_rows, stages, (int32_t*)d_plane, (int32_t*)d_tmp, st, qmax);
+}
+
+// Time each maximum pass depth 3..5 on one shape (CUDA events, best of 2
+// after a warm-up) and cache the fastest.  The planes are scratch.
+ffa_status tune_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data, int64_t m_rows,
+                     int stages, void* d_plane, void* d_tmp, cudaStream_t st, int* best_q) {
+    cudaEvent_t e0, e1;
+    FFA_CUDA_TRY(cudaEventCreate(&e0));
+    FFA_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bq = QMAX_DEFAULT;
+    ffa_status s = FFA_OK;
+    for (int q = 3; q <= 5 && s == FFA_OK; ++q) {
+        s = fold_with(d_z, precision, p0, m_data, m_rows, stages, d_plane, d_tmp, st, q);  // warm-up
+        float t_q = 1e30f;
+        for (int rep = 0; rep < 2 && s == FFA_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            s = fold_with(d_z, precision, p0, m_data, m_rows, stages, d_plane, d_tmp, st, q);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) s = cuda_fail(cudaGetLastError(), "tune_fold");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t_q = ms < t_q ? ms : t_q;
+        }
+        if (t_q < best) {
+            best = t_q;
+            bq = q;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != FFA_OK) return s;
+    int dev = 0;
+    FFA_CUDA_TRY(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[std::make_tuple(dev, precision, stages, log2i(p0))] = bq;
+    }
+    if (best_q) *best_q = bq;
+    return FFA_OK;
+}
+
 // Run the first `stages` FFA stages (all of them when stages < 0).  With
 // fewer stages the plane holds, per group of 2^stages rows, its partial
 // trials (row g * 2^stages + kappa); zero stages copy the (zero-padded) rows.
@@ -361,9 +453,8 @@ ffa_status launch_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m
     int m = 0;
     while ((1ll << m) < m_rows) ++m;
     if (stages < 0 || stages > m) stages = m;
-    if (precision == FFA_FOLD_F32)
-        return fold_impl<float>(d_z, p0, m_data, m_rows, stages, (float*)d_plane, (float*)d_tmp, st);
-    return fold_impl<int32_t>(d_z, p0, m_data, m_rows, stages, (int32_t*)d_plane, (int32_t*)d_tmp, st);
+    return fold_with(d_z, precision, p0, m_data, m_rows, stages, d_plane, d_tmp, st,
+                     tuned_qmax(precision, stages, p0));
 }
 
 }  // namespace ffa

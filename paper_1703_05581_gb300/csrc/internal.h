@@ -55,6 +55,10 @@ ffa_status launch_persist(const int32_t* d_bplane, int64_t m_rows, int64_t p0,
                           const ffa_record* d_rec, uint32_t* d_persist, cudaStream_t st);
 ffa_status launch_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
                        int64_t m_rows, int stages, void* d_plane, void* d_tmp, cudaStream_t st);
+// Time pass depths 3..5 for one fold shape and cache the fastest (used by
+// every later launch_fold of that precision, stage count and log2 p0).
+ffa_status tune_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data, int64_t m_rows,
+                     int stages, void* d_plane, void* d_tmp, cudaStream_t st, int* best_q);
 // Algorithm 1 on `count` trials starting at trial0.  fused: d_prof is the
 // plane after all but the last FFA stage (m_rows rows); the kernel applies the
 // last stage while loading.  Otherwise d_prof holds ready profiles.

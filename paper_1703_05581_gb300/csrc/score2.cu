@@ -35,6 +35,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "common.cuh"
@@ -1191,6 +1194,32 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
 
 namespace {
 
+// Resident CTAs of a kernel for a dynamic shared-memory size, times the SM
+// count, per device: queried once (launches come per base period).
+ffa_status resident_ctas(const void* fn, int threads, size_t smem, int64_t* out) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, size_t, int>, int64_t> cache;
+    int dev = 0;
+    FFA_CUDA_TRY(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(fn, smem, dev);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *out = it->second;
+            return FFA_OK;
+        }
+    }
+    int nsm = 0, per_sm = 0;
+    FFA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    FFA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+    const int64_t r = (int64_t)nsm * (per_sm < 1 ? 1 : per_sm);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = r;
+    *out = r;
+    return FFA_OK;
+}
+
 template <class C>
 size_t score2_smem_bytes(int64_t p0, int wmax, size_t elem) {
     const int64_t nbe = (p0 + wmax + C::R) / C::R + 1;
@@ -1213,12 +1242,9 @@ ffa_status launch_score2_cfg(const void* d_prof, int64_t count, int64_t trial0, 
     const void* fn = (const void*)k_score2<C, TT, FF>;
     ffa_status es = ensure_smem(fn, smem);
     if (es != FFA_OK) return es;
-    int dev = 0, nsm = 0, per_sm = 0;
-    FFA_CUDA_TRY(cudaGetDevice(&dev));
-    FFA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    FFA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, C::T, smem));
-    if (per_sm < 1) per_sm = 1;
-    const int64_t resident = (int64_t)nsm * per_sm;  // persistent: every CTA resident
+    int64_t resident = 0;  // persistent: every CTA resident
+    es = resident_ctas(fn, C::T, smem, &resident);
+    if (es != FFA_OK) return es;
     const unsigned grid = (unsigned)(count < resident ? count : resident);
     k_score2<C, TT, FF><<<grid, C::T, smem, st>>>((const TT*)d_prof, p0, m_rows, trial0, count, wd, d_rec,
                                                   d_status);
@@ -1264,12 +1290,9 @@ ffa_status launch_alg2_cfg(const void* d_prof, int64_t count, int64_t trial0, in
     const void* fn = (const void*)k_score_alg2<C, TT, FF>;
     ffa_status es = ensure_smem(fn, smem);
     if (es != FFA_OK) return es;
-    int dev = 0, nsm = 0, per_sm = 0;
-    FFA_CUDA_TRY(cudaGetDevice(&dev));
-    FFA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    FFA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, C::T, smem));
-    if (per_sm < 1) per_sm = 1;
-    const int64_t resident = (int64_t)nsm * per_sm;
+    int64_t resident = 0;
+    es = resident_ctas(fn, C::T, smem, &resident);
+    if (es != FFA_OK) return es;
     const unsigned grid = (unsigned)(count < resident ? count : resident);
     k_score_alg2<C, TT, FF><<<grid, C::T, smem, st>>>((const TT*)d_prof, p0, m_rows, trial0, count, wd,
                                                       excl_frac, d_rec);

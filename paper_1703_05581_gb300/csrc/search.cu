@@ -527,6 +527,34 @@ static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_
     return FFA_OK;
 }
 
+ffa_status ffa_autotune(const ffa_plan* p, void* d_ws, size_t ws_bytes, void* stream, int32_t* n_tuned) {
+    if (!p) return fail(FFA_ERR_ARG, "autotune: null plan");
+    if (n_tuned) *n_tuned = 0;
+    if (p->n_trials == 0) return FFA_OK;
+    if (!d_ws) return fail(FFA_ERR_ARG, "autotune: null workspace");
+    if (ws_bytes < p->ws_bytes) return fail(FFA_ERR_OOM, "autotune: workspace too small");
+    char* ws = (char*)d_ws;
+    // shapes: (stages before the fused last one, floor(log2 p0)) -> its entries
+    std::map<std::pair<int, int>, std::vector<size_t>> groups;
+    for (size_t i = 0; i < p->entries.size(); ++i) {
+        const ffa_plan_entry& e = p->entries[i];
+        int m = 0, lg = 0;
+        while ((1 << m) < e.m_rows) ++m;
+        while ((int64_t)2 << lg <= e.p0) ++lg;
+        groups[{m > 0 ? m - 1 : 0, lg}].push_back(i);
+    }
+    int32_t n = 0;
+    for (auto& g : groups) {
+        const ffa_plan_entry& e = p->entries[g.second[g.second.size() / 2]];  // the median base period
+        ffa_status s = tune_fold(ws + p->off_z, p->cfg.precision, e.p0, e.m_data, e.m_rows, g.first.first,
+                                 ws + p->off_plane0, ws + p->off_plane1, as_stream(stream), nullptr);
+        if (s != FFA_OK) return s;
+        ++n;
+    }
+    if (n_tuned) *n_tuned = n;
+    return FFA_OK;
+}
+
 ffa_status ffa_search_persistence(const ffa_plan* p, const void* d_series, void* d_ws,
                                   size_t ws_bytes, ffa_record* d_records, uint32_t* d_persist,
                                   int32_t* d_status, void* stream) {

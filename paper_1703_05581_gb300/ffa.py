@@ -93,6 +93,7 @@ _sig = {
     "ffa_search": ([_P, _P, _P, C.c_size_t, _P, _P, _P], C.c_int),
     "ffa_search_entries": ([_P, _P, _i64, _i64, _P, C.c_size_t, _P, _P, _P], C.c_int),
     "ffa_search_persistence": ([_P, _P, _P, C.c_size_t, _P, _P, _P, _P], C.c_int),
+    "ffa_autotune": ([_P, _P, C.c_size_t, _P, _P], C.c_int),
     "ffa_search_batch": ([_P, _P, _i32, _P, C.c_size_t, _P, _P, _P], C.c_int),
     "ffa_candidates": ([_P, _P, C.c_double, _i32, _P, C.c_size_t, _P, _P, _P, _P, _P, _i32],
                        C.c_int),
@@ -256,6 +257,13 @@ def search_persistence(plan: Plan, series: torch.Tensor, workspace: torch.Tensor
     _check(_lib.ffa_search_persistence(plan._h, _ptr(series), _ptr(workspace), workspace.numel(),
                                        _ptr(records), _ptr(persist), _ptr(status), _stream(stream)))
     return records, persist
+
+
+def autotune(plan: Plan, workspace: torch.Tensor, stream=None) -> int:
+    """Tune the fold's stages per pass for the plan's shapes; returns their count."""
+    n = C.c_int32()
+    _check(_lib.ffa_autotune(plan._h, _ptr(workspace), workspace.numel(), _stream(stream), C.byref(n)))
+    return n.value
 
 
 def search_entries(plan: Plan, series: torch.Tensor, entry_begin: int, entry_end: int,
