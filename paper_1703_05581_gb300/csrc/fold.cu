@@ -31,6 +31,29 @@
 namespace ffa {
 
 
+// Base periods folded by one launch: entry i has p0[i] bins, m_data[i] data
+// rows (all share m_rows), its plane at element offset off[i] of the plane
+// buffers, and owns the launch's CTAs [unit0[i], unit0[i + 1]).  A single
+// base period is a group of one.
+struct FoldGroup {
+    int32_t n;
+    int64_t p0[FOLD_GROUP_MAX];
+    int64_t m_data[FOLD_GROUP_MAX];
+    int64_t off[FOLD_GROUP_MAX];
+    int64_t unit0[FOLD_GROUP_MAX + 1];
+};
+
+// this CTA's entry and its unit within the entry
+__device__ __forceinline__ int group_entry(const FoldGroup& g, int64_t unit) {
+    int lo = 0, hi = g.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.unit0[mid] <= unit) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <class T>
 struct FoldIn;
 template <>
@@ -94,14 +117,19 @@ constexpr int FP_B = 256;
 
 template <class T, bool FIRST>
 __global__ void __launch_bounds__(FP_THREADS) k_fold_pass(const void* __restrict__ src_v,
-                                                          T* __restrict__ dst, int64_t p0,
-                                                          int64_t m_data, int s, int q, int64_t n_ct) {
+                                                          T* __restrict__ dst_all, const FoldGroup fg,
+                                                          int s, int q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int rows = 1 << q;
     const int wt = FP_B + rows - 1;
     T* buf0 = reinterpret_cast<T*>(smem_raw);
     T* buf1 = buf0 + rows * wt;
-    const int64_t unit = blockIdx.x;
+    const int ei = group_entry(fg, blockIdx.x);
+    const int64_t p0 = fg.p0[ei], m_data = fg.m_data[ei];
+    const int64_t n_ct = (p0 + FP_B - 1) / FP_B;
+    T* __restrict__ dst = dst_all + fg.off[ei];
+    if (!FIRST) src_v = (const T*)src_v + fg.off[ei];
+    const int64_t unit = blockIdx.x - fg.unit0[ei];
     const int64_t ct = unit % n_ct;
     const int64_t rest = unit / n_ct;
     const int64_t kappa = rest & ((1ll << s) - 1);
@@ -212,8 +240,8 @@ __host__ __device__ constexpr int f4_wb(int q, int q1) { return ((F4_B + (1 << q
 
 template <class T, bool FIRST, int Q1, int Q2>
 __global__ void __launch_bounds__(F4_THREADS, 2) k_fold_reg(const void* __restrict__ src_v,
-                                                           T* __restrict__ dst, int64_t p0,
-                                                           int64_t m_data, int s, int64_t n_ct) {
+                                                           T* __restrict__ dst_all, const FoldGroup fg,
+                                                           int s) {
     constexpr int q = Q1 + Q2;
     constexpr int rows = 1 << q;
     constexpr int R1 = 1 << Q1, R2 = 1 << Q2;
@@ -223,7 +251,12 @@ __global__ void __launch_bounds__(F4_THREADS, 2) k_fold_reg(const void* __restri
     T* bufA = reinterpret_cast<T*>(smem_raw);
     T* bufB = bufA + rows * WA;
 
-    const int64_t unit = blockIdx.x;
+    const int ei = group_entry(fg, blockIdx.x);
+    const int64_t p0 = fg.p0[ei], m_data = fg.m_data[ei];
+    const int64_t n_ct = (p0 + F4_B - 1) / F4_B;
+    T* __restrict__ dst = dst_all + fg.off[ei];
+    if (!FIRST) src_v = (const T*)src_v + fg.off[ei];
+    const int64_t unit = blockIdx.x - fg.unit0[ei];
     const int64_t ct = unit % n_ct;
     const int64_t rest = unit / n_ct;
     const int64_t kappa = rest & ((1ll << s) - 1);
@@ -309,48 +342,59 @@ __global__ void __launch_bounds__(F4_THREADS, 2) k_fold_reg(const void* __restri
     }
 }
 
+// Fill the group's CTA ranges for a pass whose CTAs cover `rows` output rows
+// and `tile` columns; returns the launch's CTA count.
+static int64_t group_units(FoldGroup& fg, int64_t m_rows, int rows, int tile) {
+    int64_t u = 0;
+    for (int i = 0; i < fg.n; ++i) {
+        fg.unit0[i] = u;
+        u += (m_rows / rows) * ((fg.p0[i] + tile - 1) / tile);
+    }
+    fg.unit0[fg.n] = u;
+    return u;
+}
+
 template <class T, bool FIRST, int Q1, int Q2>
-static ffa_status launch_reg(const void* src, T* dst, int64_t p0, int64_t m_rows, int64_t m_data,
-                             int s, cudaStream_t st) {
+static ffa_status launch_reg(const void* src, T* dst, FoldGroup& fg, int64_t m_rows, int s, cudaStream_t st) {
     constexpr int q = Q1 + Q2;
     constexpr int rows = 1 << q;
     const size_t smem = sizeof(T) * ((size_t)rows * f4_wa(q) + (Q2 > 0 ? (size_t)rows * f4_wb(q, Q1) : 0));
     ffa_status es = ensure_smem((const void*)k_fold_reg<T, FIRST, Q1, Q2>, smem);
     if (es != FFA_OK) return es;
-    const int64_t n_ct = (p0 + F4_B - 1) / F4_B;
-    const int64_t units = (m_rows / rows) * n_ct;
-    k_fold_reg<T, FIRST, Q1, Q2><<<(unsigned)units, F4_THREADS, smem, st>>>(src, dst, p0, m_data, s, n_ct);
+    const int64_t units = group_units(fg, m_rows, rows, F4_B);
+    if (units <= 0) return FFA_OK;
+    k_fold_reg<T, FIRST, Q1, Q2><<<(unsigned)units, F4_THREADS, smem, st>>>(src, dst, fg, s);
     FFA_LAUNCH_CHECK("k_fold_reg");
     count_launch();
     return FFA_OK;
 }
 
 template <class T, bool FIRST>
-static ffa_status pass_q(int q, const void* src, T* dst, int64_t p0, int64_t m_rows, int64_t m_data,
-                         int s, cudaStream_t st) {
+static ffa_status pass_q(int q, const void* src, T* dst, FoldGroup& fg, int64_t m_rows, int s,
+                         cudaStream_t st) {
     switch (q) {
-        case 1: return launch_reg<T, FIRST, 1, 0>(src, dst, p0, m_rows, m_data, s, st);
-        case 2: return launch_reg<T, FIRST, 2, 0>(src, dst, p0, m_rows, m_data, s, st);
-        case 3: return launch_reg<T, FIRST, 3, 0>(src, dst, p0, m_rows, m_data, s, st);
-        case 4: return launch_reg<T, FIRST, 2, 2>(src, dst, p0, m_rows, m_data, s, st);
-        case 5: return launch_reg<T, FIRST, 3, 2>(src, dst, p0, m_rows, m_data, s, st);
+        case 1: return launch_reg<T, FIRST, 1, 0>(src, dst, fg, m_rows, s, st);
+        case 2: return launch_reg<T, FIRST, 2, 0>(src, dst, fg, m_rows, s, st);
+        case 3: return launch_reg<T, FIRST, 3, 0>(src, dst, fg, m_rows, s, st);
+        case 4: return launch_reg<T, FIRST, 2, 2>(src, dst, fg, m_rows, s, st);
+        case 5: return launch_reg<T, FIRST, 3, 2>(src, dst, fg, m_rows, s, st);
         default: break;
     }
     const int rows = 1 << q;
     const size_t smem = 2 * sizeof(T) * (size_t)rows * (FP_B + rows - 1);
     ffa_status es = ensure_smem((const void*)k_fold_pass<T, FIRST>, smem);
     if (es != FFA_OK) return es;
-    const int64_t n_ct = (p0 + FP_B - 1) / FP_B;
-    const int64_t units = (m_rows / rows) * n_ct;
-    k_fold_pass<T, FIRST><<<(unsigned)units, FP_THREADS, smem, st>>>(src, dst, p0, m_data, s, q, n_ct);
+    const int64_t units = group_units(fg, m_rows, rows, FP_B);
+    if (units <= 0) return FFA_OK;
+    k_fold_pass<T, FIRST><<<(unsigned)units, FP_THREADS, smem, st>>>(src, dst, fg, s, q);
     FFA_LAUNCH_CHECK("k_fold_pass");
     count_launch();
     return FFA_OK;
 }
 
 template <class T>
-static ffa_status fold_impl(const void* d_z, int64_t p0, int64_t m_data, int64_t m_rows,
-                            int stages, T* d_plane, T* d_tmp, cudaStream_t st, int qmax) {
+static ffa_status fold_impl(const void* d_z, FoldGroup& fg, int64_t m_rows, int stages, T* d_plane, T* d_tmp,
+                            cudaStream_t st, int qmax) {
     int qs[64];
     int np = split_passes(stages, qmax, qs);
     if (np == 0) {
@@ -364,8 +408,8 @@ static ffa_status fold_impl(const void* d_z, int64_t p0, int64_t m_data, int64_t
     for (int pi = 0; pi < np; ++pi) {
         T* dst = bufs[(np - 1 - pi) & 1];
         const void* src = pi == 0 ? d_z : (const void*)bufs[(np - pi) & 1];
-        ffa_status e = pi == 0 ? pass_q<T, true>(qs[pi], src, dst, p0, m_rows, m_data, s, st)
-                               : pass_q<T, false>(qs[pi], src, dst, p0, m_rows, m_data, s, st);
+        ffa_status e = pi == 0 ? pass_q<T, true>(qs[pi], src, dst, fg, m_rows, s, st)
+                               : pass_q<T, false>(qs[pi], src, dst, fg, m_rows, s, st);
         if (e != FFA_OK) return e;
         s += qs[pi];
     }
@@ -398,11 +442,21 @@ int tuned_qmax(int precision, int stages, int64_t p0) {
 }
 }  // namespace
 
+static ffa_status fold_group(const void* d_z, int32_t precision, FoldGroup& fg, int64_t m_rows, int stages,
+                             void* d_plane, void* d_tmp, cudaStream_t st, int qmax) {
+    if (precision == FFA_FOLD_F32)
+        return fold_impl<float>(d_z, fg, m_rows, stages, (float*)d_plane, (float*)d_tmp, st, qmax);
+    return fold_impl<int32_t>(d_z, fg, m_rows, stages, (int32_t*)d_plane, (int32_t*)d_tmp, st, qmax);
+}
+
 ffa_status fold_with(const void* d_z, int32_t precision, int64_t p0, int64_t m_data, int64_t m_rows,
                      int stages, void* d_plane, void* d_tmp, cudaStream_t st, int qmax) {
-    if (precision == FFA_FOLD_F32)
-        return fold_impl<float>(d_z, p0, m_data, m_rows, stages, (float*)d_plane, (float*)d_tmp, st, qmax);
-    return fold_impl<int32_t>(d_z, p0, m_data, m_rows, stages, (int32_t*)d_plane, (int32_t*)d_tmp, st, qmax);
+    FoldGroup fg;
+    fg.n = 1;
+    fg.p0[0] = p0;
+    fg.m_data[0] = m_data;
+    fg.off[0] = 0;
+    return fold_group(d_z, precision, fg, m_rows, stages, d_plane, d_tmp, st, qmax);
 }
 
 // Time each maximum pass depth 3..5 on one shape (CUDA events, best of 2
@@ -443,6 +497,21 @@ ffa_status tune_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_d
     }
     if (best_q) *best_q = bq;
     return FFA_OK;
+}
+
+ffa_status launch_fold_group(const void* d_z, int32_t precision, int n, const int64_t* p0, const int64_t* m_data,
+                             const int64_t* off, int64_t m_rows, int stages, void* d_plane, void* d_tmp,
+                             cudaStream_t st) {
+    if (n < 1 || n > FOLD_GROUP_MAX) return fail(FFA_ERR_ARG, "fold group: 1..FOLD_GROUP_MAX base periods");
+    FoldGroup fg;
+    fg.n = n;
+    for (int i = 0; i < n; ++i) {
+        fg.p0[i] = p0[i];
+        fg.m_data[i] = m_data[i];
+        fg.off[i] = off[i];
+    }
+    return fold_group(d_z, precision, fg, m_rows, stages, d_plane, d_tmp, st,
+                      tuned_qmax(precision, stages, p0[n - 1]));
 }
 
 // Run the first `stages` FFA stages (all of them when stages < 0).  With

@@ -18,6 +18,7 @@ struct ffa_plan {
     int32_t n_octaves = 0;
     int64_t n_trials = 0;
     int64_t max_plane = 0;  // largest m_rows * p0
+    int64_t plane_elems = 0;  // elements of each plane buffer (>= max_plane; room for grouped planes)
     std::vector<ffa_plan_entry> entries;
     std::vector<int64_t> oct_first, oct_count, oct_n;
     // workspace layout (bytes)
@@ -53,6 +54,15 @@ ffa_status launch_normalise(const double* d_resid, int64_t n, int32_t precision,
 // trial's sum over its record's best window, last stage applied on the fly.
 ffa_status launch_persist(const int32_t* d_bplane, int64_t m_rows, int64_t p0,
                           const ffa_record* d_rec, uint32_t* d_persist, cudaStream_t st);
+// Base periods per grouped launch (fold, score): small planes are folded
+// and scored together so that a launch fills the GPU.
+constexpr int FOLD_GROUP_MAX = 32;
+// Fold n base periods sharing m_rows (and their tuned pass depth) in one set
+// of launches: entry i has p0[i] bins, m_data[i] rows, its plane at element
+// offset off[i] of d_plane / d_tmp.
+ffa_status launch_fold_group(const void* d_z, int32_t precision, int n, const int64_t* p0, const int64_t* m_data,
+                             const int64_t* off, int64_t m_rows, int stages, void* d_plane, void* d_tmp,
+                             cudaStream_t st);
 ffa_status launch_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
                        int64_t m_rows, int stages, void* d_plane, void* d_tmp, cudaStream_t st);
 // Time pass depths 3..5 for one fold shape and cache the fastest (used by
@@ -65,6 +75,15 @@ ffa_status tune_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_d
 ffa_status launch_score2(const void* d_prof, int32_t precision, bool fused, int64_t count,
                          int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
                          ffa_record* d_rec, int32_t* d_status, cudaStream_t st);
+// The fused scorers over a group of n base periods sharing m_rows and the
+// widths: planes at element offsets off[i] of d_plane, records of entry i at
+// d_rec + i * m_rows.
+ffa_status launch_score2_group(const void* d_plane, int32_t precision, int n, const int64_t* p0, const int64_t* off,
+                               int64_t m_rows, const ScoreWidths& wd, ffa_record* d_rec, int32_t* d_status,
+                               cudaStream_t st);
+ffa_status launch_score_alg2_group(const void* d_plane, int32_t precision, int n, const int64_t* p0,
+                                   const int64_t* off, int64_t m_rows, const ScoreWidths& wd, float excl_frac,
+                                   ffa_record* d_rec, cudaStream_t st);
 // Algorithm 2 (Section 2.2.2) with the same fused/unfused inputs.
 ffa_status launch_score_alg2(const void* d_prof, int32_t precision, bool fused, int64_t count,
                              int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,

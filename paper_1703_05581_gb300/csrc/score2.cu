@@ -496,10 +496,31 @@ __device__ __forceinline__ T width_max(const T (&c)[C::R], const Sh2<C>& sh, con
     else return wide_width<T, FIND>(c, sh, buf, tid, w, nvalid, target, first);
 }
 
-// prof: FUSED ? the stage-(m-1) plane (m_rows rows of p0) : profiles of p0.
-// Record i belongs to trial trial0 + i, i < count.
+// The base periods scored by one launch: records [t0[i], t0[i + 1]) belong
+// to entry i, whose profiles have p0[i] bins and whose plane starts at
+// element off[i] of `prof` (all share m_rows and the widths).  A single base
+// period is a group of one.
+struct ScoreGroup {
+    int32_t n;
+    int64_t t0[FOLD_GROUP_MAX + 1];
+    int32_t p0[FOLD_GROUP_MAX];
+    int64_t off[FOLD_GROUP_MAX];
+};
+
+__device__ __forceinline__ int score_entry(const ScoreGroup& g, int64_t it) {
+    int lo = 0, hi = g.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.t0[mid] <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// prof: FUSED ? the stage-(m-1) planes (m_rows rows of p0 each) : profiles of
+// p0.  Record it (< count) belongs to trial trial0 + it - t0[i] of entry i.
 template <class C, class T, bool FUSED>
-__global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ prof, int64_t p0_,
+__global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ prof_all, const ScoreGroup sg,
                                                           int64_t m_rows, int64_t trial0, int64_t count,
                                                           ScoreWidths wd, ffa_record* __restrict__ rec,
                                                           int32_t* d_status) {
@@ -508,21 +529,28 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     Sh2<C>& sh = *reinterpret_cast<Sh2<C>*>(smem_raw);
     T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(Sh2<C>) + 15) & ~(size_t)15));
     using B = BoxOps<T>;
-    const int p0 = (int)p0_;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int wmax = wd.w[wd.n - 1];
-    const int nbe = (p0 + wmax + R2) / R2 + 1;  // blocks incl. the cyclic extension
     // persistent: this CTA scores trials it, it + gridDim.x, ...
     for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
-    const int64_t k = trial0 + it;
+    const int ei = score_entry(sg, it);
+    const int64_t p0_ = sg.p0[ei];
+    const int p0 = (int)p0_;
+    const T* __restrict__ prof = prof_all + sg.off[ei];
+    const int nbe = (p0 + wmax + R2) / R2 + 1;  // blocks incl. the cyclic extension
+    const int64_t k = trial0 + (it - sg.t0[ei]);
     {
         // pull the next trial's rows towards L2 while this one is scored
-        const int64_t kn = k + gridDim.x;
         if (it + gridDim.x < count) {
-            const T* nh = FUSED ? (m_rows > 1 ? prof + (kn >> 1) * p0_ : prof) : prof + kn * p0_;
-            const T* nt = (FUSED && m_rows > 1) ? prof + ((m_rows >> 1) + (kn >> 1)) * p0_ : nullptr;
-            const int lines = (int)((p0_ * (int64_t)sizeof(T) + 127) / 128);
+            const int64_t itn = it + gridDim.x;
+            const int en = score_entry(sg, itn);
+            const int64_t pn = sg.p0[en];
+            const T* prn = prof_all + sg.off[en];
+            const int64_t kn = trial0 + (itn - sg.t0[en]);
+            const T* nh = FUSED ? (m_rows > 1 ? prn + (kn >> 1) * pn : prn) : prn + kn * pn;
+            const T* nt = (FUSED && m_rows > 1) ? prn + ((m_rows >> 1) + (kn >> 1)) * pn : nullptr;
+            const int lines = (int)((pn * (int64_t)sizeof(T) + 127) / 128);
             for (int l = tid; l < lines; l += T2) {
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(nh + l * (128 / sizeof(T))));
                 if (nt) asm volatile("prefetch.global.L2 [%0];" ::"l"(nt + l * (128 / sizeof(T))));
@@ -960,7 +988,7 @@ __device__ __forceinline__ T box_at(const T (&c)[C::R], const Sh2<C>& sh, const 
 }
 
 template <class C, class T, bool FUSED>
-__global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restrict__ prof, int64_t p0_,
+__global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restrict__ prof_all, const ScoreGroup sg,
                                                               int64_t m_rows, int64_t trial0, int64_t count,
                                                               ScoreWidths wd, float excl_frac,
                                                               ffa_record* __restrict__ rec) {
@@ -969,15 +997,18 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
     Sh2<C>& sh = *reinterpret_cast<Sh2<C>*>(smem_raw);
     T* buf = reinterpret_cast<T*>(smem_raw + ((sizeof(Sh2<C>) + 15) & ~(size_t)15));
     using B = BoxOps<T>;
-    const int p0 = (int)p0_;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int wmax = wd.w[wd.n - 1];
-    const int nbe = (p0 + wmax + R2) / R2 + 1;
-    const int h = (int)floorf(excl_frac * (float)p0 / 2.0f);
-    const int n_off = p0 - min(p0, 2 * h + 1);
     for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
-        const int64_t k = trial0 + it;
+        const int ei = score_entry(sg, it);
+        const int64_t p0_ = sg.p0[ei];
+        const int p0 = (int)p0_;
+        const T* __restrict__ prof = prof_all + sg.off[ei];
+        const int nbe = (p0 + wmax + R2) / R2 + 1;
+        const int h = (int)floorf(excl_frac * (float)p0 / 2.0f);
+        const int n_off = p0 - min(p0, 2 * h + 1);
+        const int64_t k = trial0 + (it - sg.t0[ei]);
         const T* hrow;
         const T* trow = nullptr;
         int sft = 0;
@@ -1234,8 +1265,9 @@ bool fits(int64_t p0, int wmax) {
 }
 
 template <class C, class TT, bool FF>
-ffa_status launch_score2_cfg(const void* d_prof, int64_t count, int64_t trial0, int64_t p0, int64_t m_rows,
-                             const ScoreWidths& wd, ffa_record* d_rec, int32_t* d_status, cudaStream_t st) {
+ffa_status launch_score2_cfg(const void* d_prof, const ScoreGroup& sg, int64_t count, int64_t trial0, int64_t p0,
+                             int64_t m_rows, const ScoreWidths& wd, ffa_record* d_rec, int32_t* d_status,
+                             cudaStream_t st) {
     const int wmax = wd.w[wd.n - 1];
     const size_t smem = score2_smem_bytes<C>(p0, wmax, 4);
     if (smem > 227 * 1024) return fail(FFA_ERR_UNSUPPORTED, "score: profile too long for shared memory");
@@ -1246,22 +1278,48 @@ ffa_status launch_score2_cfg(const void* d_prof, int64_t count, int64_t trial0, 
     es = resident_ctas(fn, C::T, smem, &resident);
     if (es != FFA_OK) return es;
     const unsigned grid = (unsigned)(count < resident ? count : resident);
-    k_score2<C, TT, FF><<<grid, C::T, smem, st>>>((const TT*)d_prof, p0, m_rows, trial0, count, wd, d_rec,
+    k_score2<C, TT, FF><<<grid, C::T, smem, st>>>((const TT*)d_prof, sg, m_rows, trial0, count, wd, d_rec,
                                                   d_status);
     FFA_LAUNCH_CHECK("k_score2");
     count_launch();
     return FFA_OK;
 }
 
+// p0: the longest profile of the group (it picks the CTA shape and the
+// shared-memory size)
 template <class TT, bool FF>
-ffa_status launch_score2_t(const void* d_prof, int64_t count, int64_t trial0, int64_t p0, int64_t m_rows,
-                           const ScoreWidths& wd, ffa_record* d_rec, int32_t* d_status, cudaStream_t st) {
+ffa_status launch_score2_t(const void* d_prof, const ScoreGroup& sg, int64_t count, int64_t trial0, int64_t p0,
+                           int64_t m_rows, const ScoreWidths& wd, ffa_record* d_rec, int32_t* d_status,
+                           cudaStream_t st) {
     const int wmax = wd.w[wd.n - 1];
     if (fits<Cfg<256>>(p0, wmax))
-        return launch_score2_cfg<Cfg<256>, TT, FF>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
+        return launch_score2_cfg<Cfg<256>, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
     if (fits<Cfg<512>>(p0, wmax))
-        return launch_score2_cfg<Cfg<512>, TT, FF>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
-    return launch_score2_cfg<CBig, TT, FF>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
+        return launch_score2_cfg<Cfg<512>, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
+    return launch_score2_cfg<CBig, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
+}
+
+ScoreGroup single(int64_t p0, int64_t count) {
+    ScoreGroup sg;
+    sg.n = 1;
+    sg.t0[0] = 0;
+    sg.t0[1] = count;
+    sg.p0[0] = (int32_t)p0;
+    sg.off[0] = 0;
+    return sg;
+}
+
+ffa_status score2_dispatch(const void* d_prof, const ScoreGroup& sg, int32_t precision, bool fused, int64_t count,
+                           int64_t trial0, int64_t p0max, int64_t m_rows, const ScoreWidths& wd,
+                           ffa_record* d_rec, int32_t* d_status, cudaStream_t st) {
+    if (count <= 0) return FFA_OK;
+    const int wmax = wd.w[wd.n - 1];
+    if (!fits<CBig>(p0max, wmax)) return fail(FFA_ERR_UNSUPPORTED, "score: profile longer than 32768 bins");
+    if (precision == FFA_FOLD_F32)
+        return fused ? launch_score2_t<float, true>(d_prof, sg, count, trial0, p0max, m_rows, wd, d_rec, d_status, st)
+                     : launch_score2_t<float, false>(d_prof, sg, count, trial0, p0max, m_rows, wd, d_rec, d_status, st);
+    return fused ? launch_score2_t<int32_t, true>(d_prof, sg, count, trial0, p0max, m_rows, wd, d_rec, d_status, st)
+                 : launch_score2_t<int32_t, false>(d_prof, sg, count, trial0, p0max, m_rows, wd, d_rec, d_status, st);
 }
 
 }  // namespace
@@ -1269,21 +1327,34 @@ ffa_status launch_score2_t(const void* d_prof, int64_t count, int64_t trial0, in
 ffa_status launch_score2(const void* d_prof, int32_t precision, bool fused, int64_t count,
                          int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
                          ffa_record* d_rec, int32_t* d_status, cudaStream_t st) {
-    if (count <= 0) return FFA_OK;
-    const int wmax = wd.w[wd.n - 1];
-    if (!fits<CBig>(p0, wmax)) return fail(FFA_ERR_UNSUPPORTED, "score: profile longer than 32768 bins");
-    if (precision == FFA_FOLD_F32)
-        return fused ? launch_score2_t<float, true>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st)
-                     : launch_score2_t<float, false>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
-    return fused ? launch_score2_t<int32_t, true>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st)
-                 : launch_score2_t<int32_t, false>(d_prof, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
+    return score2_dispatch(d_prof, single(p0, count), precision, fused, count, trial0, p0, m_rows, wd, d_rec,
+                           d_status, st);
+}
+
+ffa_status launch_score2_group(const void* d_plane, int32_t precision, int n, const int64_t* p0, const int64_t* off,
+                               int64_t m_rows, const ScoreWidths& wd, ffa_record* d_rec, int32_t* d_status,
+                               cudaStream_t st) {
+    if (n < 1 || n > FOLD_GROUP_MAX) return fail(FFA_ERR_ARG, "score group: 1..FOLD_GROUP_MAX base periods");
+    ScoreGroup sg;
+    sg.n = n;
+    int64_t p0max = 0;
+    for (int i = 0; i < n; ++i) {
+        sg.t0[i] = (int64_t)i * m_rows;
+        sg.p0[i] = (int32_t)p0[i];
+        sg.off[i] = off[i];
+        p0max = p0[i] > p0max ? p0[i] : p0max;
+    }
+    sg.t0[n] = (int64_t)n * m_rows;
+    return score2_dispatch(d_plane, sg, precision, true, (int64_t)n * m_rows, 0, p0max, m_rows, wd, d_rec, d_status,
+                           st);
 }
 
 namespace {
 
 template <class C, class TT, bool FF>
-ffa_status launch_alg2_cfg(const void* d_prof, int64_t count, int64_t trial0, int64_t p0, int64_t m_rows,
-                           const ScoreWidths& wd, float excl_frac, ffa_record* d_rec, cudaStream_t st) {
+ffa_status launch_alg2_cfg(const void* d_prof, const ScoreGroup& sg, int64_t count, int64_t trial0, int64_t p0,
+                           int64_t m_rows, const ScoreWidths& wd, float excl_frac, ffa_record* d_rec,
+                           cudaStream_t st) {
     const int wmax = wd.w[wd.n - 1];
     const size_t smem = score2_smem_bytes<C>(p0, wmax, 4);
     if (smem > 227 * 1024) return fail(FFA_ERR_UNSUPPORTED, "score: profile too long for shared memory");
@@ -1294,7 +1365,7 @@ ffa_status launch_alg2_cfg(const void* d_prof, int64_t count, int64_t trial0, in
     es = resident_ctas(fn, C::T, smem, &resident);
     if (es != FFA_OK) return es;
     const unsigned grid = (unsigned)(count < resident ? count : resident);
-    k_score_alg2<C, TT, FF><<<grid, C::T, smem, st>>>((const TT*)d_prof, p0, m_rows, trial0, count, wd,
+    k_score_alg2<C, TT, FF><<<grid, C::T, smem, st>>>((const TT*)d_prof, sg, m_rows, trial0, count, wd,
                                                       excl_frac, d_rec);
     FFA_LAUNCH_CHECK("k_score_alg2");
     count_launch();
@@ -1302,14 +1373,28 @@ ffa_status launch_alg2_cfg(const void* d_prof, int64_t count, int64_t trial0, in
 }
 
 template <class TT, bool FF>
-ffa_status launch_alg2_t(const void* d_prof, int64_t count, int64_t trial0, int64_t p0, int64_t m_rows,
-                         const ScoreWidths& wd, float excl_frac, ffa_record* d_rec, cudaStream_t st) {
+ffa_status launch_alg2_t(const void* d_prof, const ScoreGroup& sg, int64_t count, int64_t trial0, int64_t p0,
+                         int64_t m_rows, const ScoreWidths& wd, float excl_frac, ffa_record* d_rec,
+                         cudaStream_t st) {
     const int wmax = wd.w[wd.n - 1];
     if (fits<Cfg<256>>(p0, wmax))
-        return launch_alg2_cfg<Cfg<256>, TT, FF>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
+        return launch_alg2_cfg<Cfg<256>, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
     if (fits<Cfg<512>>(p0, wmax))
-        return launch_alg2_cfg<Cfg<512>, TT, FF>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
-    return launch_alg2_cfg<CBig, TT, FF>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
+        return launch_alg2_cfg<Cfg<512>, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
+    return launch_alg2_cfg<CBig, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
+}
+
+ffa_status alg2_dispatch(const void* d_prof, const ScoreGroup& sg, int32_t precision, bool fused, int64_t count,
+                         int64_t trial0, int64_t p0max, int64_t m_rows, const ScoreWidths& wd, float excl_frac,
+                         ffa_record* d_rec, cudaStream_t st) {
+    if (count <= 0) return FFA_OK;
+    const int wmax = wd.w[wd.n - 1];
+    if (!fits<CBig>(p0max, wmax)) return fail(FFA_ERR_UNSUPPORTED, "score: profile longer than 32768 bins");
+    if (precision == FFA_FOLD_F32)
+        return fused ? launch_alg2_t<float, true>(d_prof, sg, count, trial0, p0max, m_rows, wd, excl_frac, d_rec, st)
+                     : launch_alg2_t<float, false>(d_prof, sg, count, trial0, p0max, m_rows, wd, excl_frac, d_rec, st);
+    return fused ? launch_alg2_t<int32_t, true>(d_prof, sg, count, trial0, p0max, m_rows, wd, excl_frac, d_rec, st)
+                 : launch_alg2_t<int32_t, false>(d_prof, sg, count, trial0, p0max, m_rows, wd, excl_frac, d_rec, st);
 }
 
 }  // namespace
@@ -1317,14 +1402,26 @@ ffa_status launch_alg2_t(const void* d_prof, int64_t count, int64_t trial0, int6
 ffa_status launch_score_alg2(const void* d_prof, int32_t precision, bool fused, int64_t count,
                              int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
                              float excl_frac, ffa_record* d_rec, cudaStream_t st) {
-    if (count <= 0) return FFA_OK;
-    const int wmax = wd.w[wd.n - 1];
-    if (!fits<CBig>(p0, wmax)) return fail(FFA_ERR_UNSUPPORTED, "score: profile longer than 32768 bins");
-    if (precision == FFA_FOLD_F32)
-        return fused ? launch_alg2_t<float, true>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st)
-                     : launch_alg2_t<float, false>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
-    return fused ? launch_alg2_t<int32_t, true>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st)
-                 : launch_alg2_t<int32_t, false>(d_prof, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
+    return alg2_dispatch(d_prof, single(p0, count), precision, fused, count, trial0, p0, m_rows, wd, excl_frac,
+                         d_rec, st);
+}
+
+ffa_status launch_score_alg2_group(const void* d_plane, int32_t precision, int n, const int64_t* p0,
+                                   const int64_t* off, int64_t m_rows, const ScoreWidths& wd, float excl_frac,
+                                   ffa_record* d_rec, cudaStream_t st) {
+    if (n < 1 || n > FOLD_GROUP_MAX) return fail(FFA_ERR_ARG, "score group: 1..FOLD_GROUP_MAX base periods");
+    ScoreGroup sg;
+    sg.n = n;
+    int64_t p0max = 0;
+    for (int i = 0; i < n; ++i) {
+        sg.t0[i] = (int64_t)i * m_rows;
+        sg.p0[i] = (int32_t)p0[i];
+        sg.off[i] = off[i];
+        p0max = p0[i] > p0max ? p0[i] : p0max;
+    }
+    sg.t0[n] = (int64_t)n * m_rows;
+    return alg2_dispatch(d_plane, sg, precision, true, (int64_t)n * m_rows, 0, p0max, m_rows, wd, excl_frac,
+                         d_rec, st);
 }
 
 }  // namespace ffa

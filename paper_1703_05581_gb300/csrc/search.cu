@@ -262,6 +262,12 @@ struct PhaseTimer {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// grouping of small base periods (see group_end)
+constexpr int64_t GROUP_TRIALS = 1024;
+constexpr int64_t GROUP_ELEMS = (int64_t)1 << 24;
+// elements a base period's plane takes in a group (256-byte aligned)
+static size_t plane_slot(const ffa_plan_entry& e) { return ((size_t)e.m_rows * e.p0 + 63) & ~(size_t)63; }
+
 extern "C" {
 
 const char* ffa_status_string(ffa_status s) {
@@ -400,10 +406,17 @@ ffa_status ffa_plan_create(const ffa_search_config* cfg, int64_t n, ffa_plan** o
     off = align256(off + (cfg->precision == FFA_FOLD_F32 ? 4 : 1) * (size_t)n0);
     p->off_stats = off;
     off = align256(off + sizeof(double) * STATS_DOUBLES);
+    // planes: the largest base period, or a group of small ones (GROUP_ELEMS)
+    p->plane_elems = std::max<int64_t>(p->max_plane, 1);
+    for (const ffa_plan_entry& e : p->entries)
+        if (e.m_rows < GROUP_TRIALS) {
+            const int64_t want = (GROUP_TRIALS / e.m_rows) * (int64_t)plane_slot(e);
+            p->plane_elems = std::max<int64_t>(p->plane_elems, std::min<int64_t>(want, GROUP_ELEMS));
+        }
     p->off_plane0 = off;
-    off = align256(off + 4 * (size_t)std::max<int64_t>(p->max_plane, 1));
+    off = align256(off + 4 * (size_t)p->plane_elems);
     p->off_plane1 = off;
-    off = align256(off + 4 * (size_t)std::max<int64_t>(p->max_plane, 1));
+    off = align256(off + 4 * (size_t)p->plane_elems);
     p->off_cand = off;
     off = align256(off + sizeof(CandCtl) + 256 + sizeof(unsigned long long) * CAND_MAX +
                    sizeof(CandOut) * CAND_MAX);
@@ -439,6 +452,34 @@ ffa_status ffa_plan_entries(const ffa_plan* p, ffa_plan_entry* out, int64_t cap)
 // The pipeline for plan entries [e0, e1): every octave holding one of them is
 // prepared (downsampled, dereddened, normalised); only those base periods are
 // folded and scored.
+// Consecutive base periods folded and scored by one set of launches: same
+// octave, rows, widths and floor(log2 p0) (so the same tuned pass depth and
+// CTA shape), together fewer than GROUP_TRIALS trials and within the plane
+// buffers.  Base periods of GROUP_TRIALS rows or more go alone.
+
+static int64_t group_end(const ffa_plan* p, int64_t t, int64_t b) {
+    const ffa_plan_entry& e0 = p->entries[(size_t)t];
+    if (e0.m_rows >= GROUP_TRIALS) return t + 1;
+    auto lg = [](int64_t v) {
+        int r = 0;
+        while ((int64_t)2 << r <= v) ++r;
+        return r;
+    };
+    int64_t j = t, trials = 0;
+    size_t elems = 0;
+    while (j < b && j - t < FOLD_GROUP_MAX) {
+        const ffa_plan_entry& e = p->entries[(size_t)j];
+        if (e.octave != e0.octave || e.m_rows != e0.m_rows || lg(e.p0) != lg(e0.p0) || e.n_widths != e0.n_widths ||
+            std::memcmp(e.widths, e0.widths, sizeof(int32_t) * (size_t)e0.n_widths) != 0)
+            break;
+        if (elems + plane_slot(e) > (size_t)p->plane_elems || trials + e.m_rows > GROUP_TRIALS) break;
+        elems += plane_slot(e);
+        trials += e.m_rows;
+        ++j;
+    }
+    return j > t ? j : t + 1;
+}
+
 static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_ws, size_t ws_bytes,
                                ffa_record* d_records, int32_t* d_status, cudaStream_t st, int64_t e0,
                                int64_t e1, uint32_t* d_persist = nullptr) {
@@ -487,10 +528,51 @@ static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_
         PhaseTimer fold_t(1, o, st);
         const int64_t a = std::max<int64_t>(e0, p->oct_first[o]);
         const int64_t b = std::min<int64_t>(e1, p->oct_first[o] + p->oct_count[o]);
-        for (int64_t t = a; t < b; ++t) {
+        for (int64_t t = a; t < b;) {
+            const int64_t t1 = group_end(p, t, b);
             const ffa_plan_entry& e = p->entries[(size_t)t];
             int m = 0;
             while ((1 << m) < e.m_rows) ++m;
+            ScoreWidths wd;
+            wd.n = e.n_widths;
+            for (int k = 0; k < 16; ++k) wd.w[k] = e.widths[k];
+            const float excl = c.alg2_window > 0.0f ? c.alg2_window : 0.2f;
+            if (t1 - t > 1) {
+                // a group of small base periods: one set of fold launches, one scorer launch
+                const int n = (int)(t1 - t);
+                int64_t p0s[FOLD_GROUP_MAX], mds[FOLD_GROUP_MAX], offs[FOLD_GROUP_MAX];
+                int64_t off = 0;
+                for (int i = 0; i < n; ++i) {
+                    const ffa_plan_entry& ei = p->entries[(size_t)(t + i)];
+                    p0s[i] = ei.p0;
+                    mds[i] = ei.m_data;
+                    offs[i] = off;
+                    off += (int64_t)plane_slot(ei);
+                }
+                s = launch_fold_group(z, c.precision, n, p0s, mds, offs, e.m_rows, m > 0 ? m - 1 : 0, plane0,
+                                      plane1, st);
+                if (s != FFA_OK) return s;
+                if (c.scorer == FFA_SCORE_ALG2)
+                    s = launch_score_alg2_group(plane0, c.precision, n, p0s, offs, e.m_rows, wd, excl,
+                                                d_records + e.first_trial, st);
+                else
+                    s = launch_score2_group(plane0, c.precision, n, p0s, offs, e.m_rows, wd,
+                                            d_records + e.first_trial, d_status, st);
+                if (s != FFA_OK) return s;
+                if (d_persist) {
+                    s = launch_fold_group(bits, FFA_FOLD_I8, n, p0s, mds, offs, e.m_rows, m > 0 ? m - 1 : 0, plane0,
+                                          plane1, st);
+                    if (s != FFA_OK) return s;
+                    for (int i = 0; i < n; ++i) {
+                        const ffa_plan_entry& ei = p->entries[(size_t)(t + i)];
+                        s = launch_persist((const int32_t*)plane0 + offs[i], ei.m_rows, ei.p0,
+                                           d_records + ei.first_trial, d_persist + ei.first_trial, st);
+                        if (s != FFA_OK) return s;
+                    }
+                }
+                t = t1;
+                continue;
+            }
             // per-kernel timing of every TIMING_SAMPLE-th base period of an octave
             const bool sample = ((t - p->oct_first[o]) % TIMING_SAMPLE) == 0;
             // all but the last stage; the scorer applies the last one while loading
@@ -499,13 +581,9 @@ static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_
                             plane1, st);
             if (s != FFA_OK) return s;
             fold_k.stop();
-            ScoreWidths wd;
-            wd.n = e.n_widths;
-            for (int k = 0; k < 16; ++k) wd.w[k] = e.widths[k];
             PhaseTimer score_k(3, o, st, sample);
             if (c.scorer == FFA_SCORE_ALG2)
-                s = launch_score_alg2(plane0, c.precision, true, e.m_rows, 0, e.p0, e.m_rows, wd,
-                                      c.alg2_window > 0.0f ? c.alg2_window : 0.2f,
+                s = launch_score_alg2(plane0, c.precision, true, e.m_rows, 0, e.p0, e.m_rows, wd, excl,
                                       d_records + e.first_trial, st);
             else
                 s = launch_score2(plane0, c.precision, true, e.m_rows, 0, e.p0, e.m_rows, wd,
@@ -521,6 +599,7 @@ static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_
                                    d_persist + e.first_trial, st);
                 if (s != FFA_OK) return s;
             }
+            ++t;
         }
         fold_t.stop();
     }

@@ -64,6 +64,13 @@ def units(cfg, n) -> float:
     return float(np.sum(e["m_data"].astype(np.float64) * e["p0"] * e["m_rows"]))
 
 
+def profile_bins(cfg, n) -> float:
+    """Folded-profile bins a request scores (M * P0 per base period): the
+    work of the fold's last stage and of the scorer, whatever the rows."""
+    e = ffa.Plan(cfg, n).entries
+    return float(np.sum(e["p0"].astype(np.float64) * e["m_rows"]))
+
+
 def run(rate: float, count: int, budget: int, slots: int, seed: int) -> dict:
     pool = torch.empty(1 << 26, dtype=torch.float32).pin_memory().numpy()
     pool[:] = np.random.default_rng(seed).standard_normal(pool.size, dtype=np.float32)
@@ -104,12 +111,14 @@ def run(rate: float, count: int, budget: int, slots: int, seed: int) -> dict:
     done.set()
     srv.close()
     tot_units = sum(units(c, x.size) for _, c, x in reqs)
+    tot_bins = sum(profile_bins(c, x.size) for _, c, x in reqs)
     lat = np.array(lat)
     return {
         "metric": "FFA serving latency", "offered_rate_req_s": rate, "requests": len(reqs),
         "slots": slots, "budget_bytes": budget, "peak_arena_bytes": int(peak_used[0]),
         "wall_s": wall, "throughput_req_s": len(reqs) / wall,
         "throughput_samples_trials_s": tot_units / wall,
+        "throughput_profile_bins_s": tot_bins / wall,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "mean": float(lat.mean())},
         "queued_ms_p50": float(np.percentile(qd, 50)), "running_ms_p50": float(np.percentile(runs, 50)),
