@@ -7,8 +7,8 @@
 // registers.  Blocks beyond the first T (the cyclic extension) only take part
 // in the prefix step.  The CTA shape (T threads of R bins) follows the
 // profile length: 256 x 8 up to 2048 bins (several CTAs per SM), 512 x 16 up
-// to 8192, 1024 x 32 up to 32768 (one per SM), so that short profiles do not
-// leave most of a CTA idle.
+// to 8192, 1024 x 16 up to 16384, 1024 x 32 up to 32768 (one per SM), so that
+// short profiles do not leave most of a CTA idle.
 //
 // Median and MAD (exact).  A monotone bucket function (affine map of the
 // value, rounded, clamped) feeds a shared-memory histogram; the
@@ -49,7 +49,8 @@ namespace {
 
 // CTA shapes.  A profile of p0 bins is cut into blocks of R bins, one per
 // thread; T * R >= p0.  Long profiles take 1024-thread CTAs, one per SM;
-// short ones smaller CTAs, several per SM, each on its own profile.
+// short ones smaller CTAs, several per SM, each on its own profile.  The
+// shape is the first of 256 x 8, 512 x 16, 1024 x 16, 1024 x 32 that fits.
 template <int TH>
 struct Cfg;
 template <>
@@ -63,6 +64,11 @@ struct Cfg<512> {
 template <>
 struct Cfg<256> {
     static constexpr int T = 256, R = 8, MAXB = 512, NBK = 512, CAPM = 512, MINB = 4;
+};
+// 1024 threads of 16 bins: profiles of 8193..16384 bins, which would leave
+// half or more of a 1024 x 32 CTA idle
+struct CMid {
+    static constexpr int T = 1024, R = 16, MAXB = 2048, NBK = 2048, CAPM = 1024, MINB = 1;
 };
 using CBig = Cfg<1024>;
 constexpr double KMAD = 1.4826;   // printed after Eq. 4
@@ -905,21 +911,42 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         if (lane == 0) sh.bw_max[wi] = Bw;
     }
     __syncthreads();
-    // S/N_w = (B_w - w*med) / (K*MAD*sqrt(w)) in FP64.  Widths are ranked with
-    // one shared reciprocal (within a few ulp of the quotient); the winner's
-    // S/N is then the correctly rounded quotient (round-to-nearest intrinsics,
-    // no contraction).  Ties go to the smaller width.
+    // S/N_w = (B_w - w*med) / (K*MAD*sqrt(w)).  sqrt(w) for w = 2^n is
+    // 2^(n/2), or 2^((n-1)/2) times the correctly rounded sqrt(2) for odd n
+    // (the correctly rounded square root, without computing one).  Int
+    // profiles: FP64 with round-to-nearest intrinsics, the correctly rounded
+    // quotient of the exact numerator (widths ranked by an FP32 key first).
+    // Float profiles: the numerator in float-float (med split into two
+    // floats; w * part is exact) and one FP32 division, within a few ulp of
+    // the FP64 quotient (GB300's FP64 rate is a small fraction of FP32's).
+    // Ties go to the smaller width.
     if (warp == 0) {
         const double kmad = __dmul_rn(KMAD, mad);
-        // ranking key (FP32): numerator formed in FP64 then scaled by 1/sqrt(w)
+        constexpr double SQRT2 = 1.4142135623730951;  // sqrt(2) rounded to nearest
         float key = -INFINITY;
-        if (lane < wd.n) {
-            const double w = (double)wd.w[lane];
-            const double num = __dsub_rn(sh.bw_max[lane], __dmul_rn(w, med));
-            const int n = __ffs(wd.w[lane]) - 1;
-            // 1/sqrt(w) for w = 2^n: 2^(-n/2) for even n, else 2^(-(n-1)/2)/sqrt(2)
-            const float rs = (n & 1) ? ldexpf(0.70710678f, -(n - 1) / 2) : ldexpf(1.0f, -n / 2);
-            key = __double2float_rn(num) * rs;
+        if constexpr (Traits<T>::is_int) {
+            if (lane < wd.n) {
+                const double w = (double)wd.w[lane];
+                const double num = __dsub_rn(sh.bw_max[lane], __dmul_rn(w, med));
+                const int n = __ffs(wd.w[lane]) - 1;
+                // 1/sqrt(w) for w = 2^n: 2^(-n/2) for even n, else 2^(-(n-1)/2)/sqrt(2)
+                const float rs = (n & 1) ? ldexpf(0.70710678f, -(n - 1) / 2) : ldexpf(1.0f, -n / 2);
+                key = __double2float_rn(num) * rs;
+            }
+        } else {
+            const float mh = __double2float_rn(med);
+            const float ml = __double2float_rn(__dsub_rn(med, (double)mh));
+            const float kf = __double2float_rn(kmad);
+            if (lane < wd.n) {
+                const float w = (float)wd.w[lane];
+                const float bx = (float)sh.bw_max[lane];
+                float hi, lo;
+                two_sum(bx, -(w * mh), hi, lo);  // w * mh, w * ml exact (w a power of two)
+                const float num = __fadd_rn(hi, __fsub_rn(lo, w * ml));
+                const int n = __ffs(wd.w[lane]) - 1;
+                const float sq = (n & 1) ? (float)ldexp(SQRT2, (n - 1) / 2) : ldexpf(1.0f, n / 2);
+                key = __fdiv_rn(num, __fmul_rn(kf, sq));
+            }
         }
         int bw = lane;
         for (int o = 16; o > 0; o >>= 1) {
@@ -931,10 +958,15 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
             }
         }
         if (lane == 0) {
-            const double w = (double)wd.w[bw];
-            const double num = __dsub_rn(sh.bw_max[bw], __dmul_rn(w, med));
-            const double den = __dmul_rn(kmad, __dsqrt_rn(w));
-            sh.dred[0] = __ddiv_rn(num, den);
+            if constexpr (Traits<T>::is_int) {
+                const int n = __ffs(wd.w[bw]) - 1;
+                const double w = (double)wd.w[bw];
+                const double num = __dsub_rn(sh.bw_max[bw], __dmul_rn(w, med));
+                const double sq = (n & 1) ? ldexp(SQRT2, (n - 1) / 2) : ldexp(1.0, n / 2);
+                sh.dred[0] = __ddiv_rn(num, __dmul_rn(kmad, sq));
+            } else {
+                sh.dred[0] = (double)key;
+            }
             sh.ired[0] = bw;
         }
     }
@@ -1187,7 +1219,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
                 w1 += __shfl_xor_sync(0xffffffffu, w1, o);
                 w2 += __shfl_xor_sync(0xffffffffu, w2, o);
             }
-            if (n_off >= 2) {
+            if (tid == 0 && n_off >= 2) {  // only thread 0 keeps the score: FP64 once per width
                 const double a1 = ((double)s1 - (double)w1) / n_off;        // mean offset from ref
                 const double var = ((double)s2 - (double)w2) / n_off - a1 * a1;
                 const double sd = var > 0.0 ? sqrt(var) : 0.0;
@@ -1296,6 +1328,8 @@ ffa_status launch_score2_t(const void* d_prof, const ScoreGroup& sg, int64_t cou
         return launch_score2_cfg<Cfg<256>, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
     if (fits<Cfg<512>>(p0, wmax))
         return launch_score2_cfg<Cfg<512>, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
+    if (fits<CMid>(p0, wmax))
+        return launch_score2_cfg<CMid, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
     return launch_score2_cfg<CBig, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
 }
 
@@ -1381,6 +1415,8 @@ ffa_status launch_alg2_t(const void* d_prof, const ScoreGroup& sg, int64_t count
         return launch_alg2_cfg<Cfg<256>, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
     if (fits<Cfg<512>>(p0, wmax))
         return launch_alg2_cfg<Cfg<512>, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
+    if (fits<CMid>(p0, wmax))
+        return launch_alg2_cfg<CMid, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
     return launch_alg2_cfg<CBig, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
 }
 

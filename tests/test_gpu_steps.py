@@ -189,7 +189,9 @@ def _check_records(got, ref, profiles, tol):
                                        (2048, tuple(2 ** i for i in range(12))),
                                        (4093, tuple(2 ** i for i in range(11))),
                                        (8192, tuple(2 ** i for i in range(12))),
+                                       (10007, tuple(2 ** i for i in range(12))),
                                        (15625, tuple(2 ** i for i in range(12))),
+                                       (16384, tuple(2 ** i for i in range(13))),
                                        (31249, tuple(2 ** i for i in range(13))),
                                        (32768, tuple(2 ** i for i in range(14)))])
 def test_score_float(F, orc, dev, p0, widths):
@@ -209,6 +211,7 @@ def test_score_float(F, orc, dev, p0, widths):
 @pytest.mark.parametrize("p0,widths", [(5, (1, 2, 4)), (256, (1, 2, 4, 8, 16)),
                                        (1953, tuple(2 ** i for i in range(10))),
                                        (6000, tuple(2 ** i for i in range(11))),
+                                       (12000, tuple(2 ** i for i in range(12))),
                                        (15625, tuple(2 ** i for i in range(12)))])
 def test_score_int_bit_exact(F, orc, dev, p0, widths):
     rng = np.random.default_rng(p0 + 1)
