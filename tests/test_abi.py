@@ -112,3 +112,18 @@ def test_workspace_covers_buffers(ffa):
     n0 = 1 << 26
     biggest = int((plan.entries["m_rows"].astype(np.int64) * plan.entries["p0"]).max())
     assert plan.workspace_bytes >= 8 * n0 * 2 + 4 * n0 + 8 * biggest
+
+
+def test_server_request_bytes(ffa):
+    """Arena bytes of a serving request (host only): series, periodogram and
+    workspace, each rounded up to 256 bytes."""
+    al = lambda x: (x + 255) // 256 * 256
+    for n, kw in CONFIGS[:4]:
+        for prec in (0, 1):
+            cfg = ffa.Config(**kw, precision=prec)
+            plan = ffa.Plan(cfg, n)
+            want = al(4 * n) + al(16 * max(plan.n_trials, 1)) + al(plan.workspace_bytes)
+            assert ffa.request_bytes(cfg, n) == want
+    u8 = ffa.Config(**CONFIGS[0][1], in_type=ffa.IN_U8)
+    plan = ffa.Plan(u8, 65536)
+    assert ffa.request_bytes(u8, 65536) == al(65536) + al(16 * plan.n_trials) + al(plan.workspace_bytes)
