@@ -99,6 +99,8 @@ struct Sh2 {
     int ired2[C::CAPM];      // gathered int values
     unsigned long long ukey[2];
     uint32_t cnt, below;
+    float mthr[4];  // MAD bracket: |x - med| <= D1 <=> mthr[0] <= x <= mthr[1]; D2: mthr[2], mthr[3]
+    int mok;
     int bin_a, bin_b;
     uint32_t below_a, below_b;
     int phase;
@@ -241,8 +243,9 @@ __device__ void blk_exscan_ff(float vh, Sh2<C>& sh, float& oh, float& ol, float&
     __syncthreads();
 }
 
-// ranks ra <= rb -> their bins and the counts below those bins, one scan
-template <class C>
+// ranks ra <= rb -> their bins and the counts below those bins, one scan.
+// PREFIX: also leave in hist[b] the count of every bin before b.
+template <bool PREFIX = false, class C>
 __device__ void blk_find2(Sh2<C>& sh, uint32_t ra, uint32_t rb) {
     FFA_CFG_ALIASES
     const int per = NBK / T2;
@@ -261,6 +264,7 @@ __device__ void blk_find2(Sh2<C>& sh, uint32_t ra, uint32_t rb) {
             sh.bin_b = b0 + t;
             sh.below_b = c;
         }
+        if (PREFIX) sh.hist[b0 + t] = c;  // each thread rewrites only the bins it read
         c += h;
     }
     __syncthreads();
@@ -283,7 +287,10 @@ template <class C>
 __device__ void cand_pick2(Sh2<C>& sh, uint32_t n, uint32_t ta, uint32_t tb, unsigned long long* ka,
                            unsigned long long* kb) {
     FFA_CFG_ALIASES
-    for (uint32_t i = threadIdx.x; i < n; i += T2) sh.hist[i] = 0;
+    // rank counters in ired2 (the int gather buffer, already turned into keys):
+    // the median histogram stays intact for the MAD bracket
+    uint32_t* rank = reinterpret_cast<uint32_t*>(sh.ired2);
+    for (uint32_t i = threadIdx.x; i < n; i += T2) rank[i] = 0;
     __syncthreads();
     const uint32_t chunks = (T2 + n - 1) / (n ? n : 1);  // threads per candidate
     const uint32_t pairs = n * chunks;
@@ -295,11 +302,11 @@ __device__ void cand_pick2(Sh2<C>& sh, uint32_t n, uint32_t ta, uint32_t tb, uns
             const unsigned long long cj = sh.cand[j];
             rk += (cj < ci) || (cj == ci && j < i);
         }
-        if (rk) atomicAdd(&sh.hist[i], rk);
+        if (rk) atomicAdd(&rank[i], rk);
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < n; i += T2) {
-        const uint32_t rk = sh.hist[i];
+        const uint32_t rk = rank[i];
         if (rk == ta) sh.ukey[0] = sh.cand[i];
         if (rk == tb) sh.ukey[1] = sh.cand[i];
     }
@@ -650,7 +657,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
             if (r < nvalid) atomicAdd(&sh.hist[bucket_m(x[r])], 1u);
     }
     __syncthreads();
-    blk_find2(sh, r1, r2);
+    blk_find2<true>(sh, r1, r2);  // hist becomes the prefix counts of the bins
     const int mb1 = sh.bin_a, mb2 = sh.bin_b;
     const uint32_t mbelow = sh.below_a;
     if (nvalid > 0) {
@@ -669,8 +676,10 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     }
     __syncthreads();
     double med;
+    bool med_hist;  // the median came from the histogram (its prefix counts are in hist)
     {
         const uint32_t cc = sh.cnt;
+        med_hist = cc <= CAPM;
         for (uint32_t i = tid; i < cc && i < CAPM; i += T2) {
             if constexpr (Traits<T>::is_int) sh.cand[i] = ikey(sh.ired2[i]);
             else sh.cand[i] = fkey(sh.candf[i]);
@@ -710,7 +719,115 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     }
 
     // ---- MAD (Eq. 3), exact ----
-    double mad;
+    double mad = 0.0;
+    bool mad_done = false;
+    if constexpr (!Traits<T>::is_int) {
+        // Bracket from the median histogram.  With B the (monotone) bucket map
+        // and N(d) = #{x : |x - med| <= d}, every such x has B(lo) <= B(x) <=
+        // B(hi) for lo, hi = med -+ d rounded to float, and every x with
+        // B(lo) < B(x) < B(hi) is such an x; the prefix counts of the buckets
+        // give U(d) >= N(d) >= L(d).  So the r1-th smallest deviation exceeds
+        // any d with U(d) <= r1 (D1) and the r2-th is at most any d with
+        // L(d) > r2 (D2): only samples with D1 < |x - med| <= D2 are gathered,
+        // classified exactly by float bounds of med -+ D (directed rounding).
+        if (med_hist) {
+            if (warp < 2) {  // warp 0 finds D1, warp 1 finds D2
+                const double hstep = 0.5 / (double)inv_m;  // half a bucket
+                const int K = NBK;                         // d up to 4 sigma
+                auto pb = [&](int b) -> uint32_t { return b >= NBK ? (uint32_t)p0 : sh.hist[b]; };
+                auto lu = [&](int k, uint32_t& L, uint32_t& U) {
+                    const double d = (double)k * hstep;
+                    const int bl = fbucket<NBK>(__double2float_rn(__dsub_rn(med, d)), mean, inv_m);
+                    const int bh = fbucket<NBK>(__double2float_rn(__dadd_rn(med, d)), mean, inv_m);
+                    U = pb(bh + 1) - pb(bl);
+                    L = bh - 1 >= bl + 1 ? pb(bh) - pb(bl + 1) : 0u;
+                };
+                // first k in [0, K] where a monotone predicate holds (K + 1: none)
+                auto first_true = [&](auto pred) -> int {
+                    int a = 0, b = K + 1;
+                    while (a < b) {
+                        const int step = (b - a + 31) / 32;
+                        const int k = a + lane * step;
+                        const unsigned m = __ballot_sync(0xffffffffu, k < b && pred(k));
+                        if (m == 0) {
+                            a = min(b, a + 32 * step);
+                        } else {
+                            const int f = __ffs(m) - 1;
+                            b = a + f * step;
+                            a = f == 0 ? a : a + (f - 1) * step + 1;
+                        }
+                    }
+                    return b;
+                };
+                if (warp == 0) {
+                    const int kA = first_true([&](int k) {
+                        uint32_t L, U;
+                        lu(k, L, U);
+                        return U > r1;
+                    }) - 1;
+                    if (lane == 0) {
+                        if (kA >= 0) {
+                            const double d1 = (double)kA * hstep;
+                            sh.mthr[0] = __double2float_ru(__dsub_ru(med, d1));
+                            sh.mthr[1] = __double2float_rd(__dadd_rd(med, d1));
+                        } else {
+                            sh.mthr[0] = INFINITY;
+                            sh.mthr[1] = -INFINITY;
+                        }
+                    }
+                } else {
+                    const int kB = first_true([&](int k) {
+                        uint32_t L, U;
+                        lu(k, L, U);
+                        return L >= r2 + 1;
+                    });
+                    if (lane == 0) {
+                        sh.mok = kB <= K;
+                        const double d2 = (double)(kB <= K ? kB : K) * hstep;
+                        sh.mthr[2] = __double2float_ru(__dsub_ru(med, d2));
+                        sh.mthr[3] = __double2float_rd(__dadd_rd(med, d2));
+                    }
+                }
+            }
+            if (tid == 0) {
+                sh.cnt = 0;
+                sh.below = 0;
+            }
+            __syncthreads();
+            if (sh.mok) {
+                const float l1 = sh.mthr[0], h1 = sh.mthr[1], l2 = sh.mthr[2], h2 = sh.mthr[3];
+                uint32_t nbel = 0;
+                if (nvalid > 0) {
+#pragma unroll
+                    for (int r = 0; r < R2; ++r)
+                        if (r < nvalid) {
+                            const float v = (float)x[r];
+                            if (v >= l1 && v <= h1) {
+                                ++nbel;
+                            } else if (v >= l2 && v <= h2) {
+                                const uint32_t q = atomicAdd(&sh.cnt, 1u);
+                                if (q < CAPM) sh.candf[q] = v;
+                            }
+                        }
+                }
+                nbel = __reduce_add_sync(0xffffffffu, nbel);
+                if (lane == 0 && nbel) atomicAdd(&sh.below, nbel);
+                __syncthreads();
+                const uint32_t cc = sh.cnt, cb = sh.below;
+                if (cc <= CAPM && cb <= r1 && r2 - cb < cc) {
+                    for (uint32_t i = tid; i < cc; i += T2) sh.cand[i] = dkey(fabs((double)sh.candf[i] - med));
+                    __syncthreads();
+                    unsigned long long k1, k2;
+                    cand_pick2(sh, cc, r1 - cb, r2 - cb, &k1, &k2);
+                    const double d1 = dkey_inv(k1), d2 = dkey_inv(k2);
+                    mad = (r1 == r2) ? d1 : (d1 + d2) / 2;
+                    mad_done = true;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if (!mad_done) {
     for (int b = tid; b < NBK; b += T2) sh.hist[b] = 0;
     if (tid == 0) {
         sh.cnt = 0;
@@ -826,6 +943,8 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         }
         __syncthreads();
     }
+
+    }  // !mad_done
 
     // ---- blocked cyclic prefix (bins past p0 repeat the profile) ----
     // Extension blocks (index >= T2) start at bin 32768 > p0, above the value
