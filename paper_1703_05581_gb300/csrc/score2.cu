@@ -100,6 +100,7 @@ struct Sh2 {
     unsigned long long ukey[2];
     uint32_t cnt, below;
     float mthr[4];  // MAD bracket: |x - med| <= D1 <=> mthr[0] <= x <= mthr[1]; D2: mthr[2], mthr[3]
+    long long mthri[4];  // the same bounds for int profiles
     int mok;
     int bin_a, bin_b;
     uint32_t below_a, below_b;
@@ -721,6 +722,110 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     // ---- MAD (Eq. 3), exact ----
     double mad = 0.0;
     bool mad_done = false;
+    if constexpr (Traits<T>::is_int) {
+        // The same bracket in integers: the deviation is e / 2 with the exact
+        // integer e = |2x - s2| (s2 = 2 med), and |2x - s2| <= E exactly when
+        // ceil((s2 - E) / 2) <= x <= floor((s2 + E) / 2).
+        if (med_hist) {
+            const long long s2 = llrint(2.0 * med);
+            const long long estep = 1ll << ish;  // half a bucket in units of e
+            if (warp < 2) {
+                const int K = NBK;
+                auto pb = [&](int b) -> uint32_t { return b >= NBK ? (uint32_t)p0 : sh.hist[b]; };
+                auto clampi = [](long long v) -> int {
+                    return v < INT32_MIN ? INT32_MIN : (v > INT32_MAX ? INT32_MAX : (int)v);
+                };
+                auto lu = [&](int k, uint32_t& L, uint32_t& U) {
+                    const long long E = (long long)k * estep;
+                    const long long xl = (s2 - E + 1) >> 1, xh = (s2 + E) >> 1;  // ceil, floor
+                    const int bl = ibucket<NBK>(clampi(xl), ibase, ish);
+                    const int bh = ibucket<NBK>(clampi(xh), ibase, ish);
+                    U = xl <= xh ? pb(bh + 1) - pb(bl) : 0u;
+                    L = bh - 1 >= bl + 1 ? pb(bh) - pb(bl + 1) : 0u;
+                };
+                auto first_true = [&](auto pred) -> int {
+                    int a = 0, b = K + 1;
+                    while (a < b) {
+                        const int step = (b - a + 31) / 32;
+                        const int k = a + lane * step;
+                        const unsigned m = __ballot_sync(0xffffffffu, k < b && pred(k));
+                        if (m == 0) {
+                            a = min(b, a + 32 * step);
+                        } else {
+                            const int f = __ffs(m) - 1;
+                            b = a + f * step;
+                            a = f == 0 ? a : a + (f - 1) * step + 1;
+                        }
+                    }
+                    return b;
+                };
+                if (warp == 0) {
+                    const int kA = first_true([&](int k) {
+                        uint32_t L, U;
+                        lu(k, L, U);
+                        return U > r1;
+                    }) - 1;
+                    if (lane == 0) {
+                        if (kA >= 0) {
+                            const long long E1 = (long long)kA * estep;
+                            sh.mthri[0] = (s2 - E1 + 1) >> 1;
+                            sh.mthri[1] = (s2 + E1) >> 1;
+                        } else {
+                            sh.mthri[0] = 1;
+                            sh.mthri[1] = 0;  // empty
+                        }
+                    }
+                } else {
+                    const int kB = first_true([&](int k) {
+                        uint32_t L, U;
+                        lu(k, L, U);
+                        return L >= r2 + 1;
+                    });
+                    if (lane == 0) {
+                        sh.mok = kB <= K;
+                        const long long E2 = (long long)(kB <= K ? kB : K) * estep;
+                        sh.mthri[2] = (s2 - E2 + 1) >> 1;
+                        sh.mthri[3] = (s2 + E2) >> 1;
+                    }
+                }
+            }
+            if (tid == 0) {
+                sh.cnt = 0;
+                sh.below = 0;
+            }
+            __syncthreads();
+            if (sh.mok) {
+                const long long l1 = sh.mthri[0], h1 = sh.mthri[1], l2 = sh.mthri[2], h2 = sh.mthri[3];
+                uint32_t nbel = 0;
+                if (nvalid > 0) {
+#pragma unroll
+                    for (int r = 0; r < R2; ++r)
+                        if (r < nvalid) {
+                            const long long v = (long long)x[r];
+                            if (v >= l1 && v <= h1) {
+                                ++nbel;
+                            } else if (v >= l2 && v <= h2) {
+                                const uint32_t q = atomicAdd(&sh.cnt, 1u);
+                                const long long e = 2 * v - s2;
+                                if (q < CAPM) sh.cand[q] = (unsigned long long)(e < 0 ? -e : e);
+                            }
+                        }
+                }
+                nbel = __reduce_add_sync(0xffffffffu, nbel);
+                if (lane == 0 && nbel) atomicAdd(&sh.below, nbel);
+                __syncthreads();
+                const uint32_t cc = sh.cnt, cb = sh.below;
+                if (cc <= CAPM && cb <= r1 && r2 - cb < cc) {
+                    unsigned long long k1, k2;
+                    cand_pick2(sh, cc, r1 - cb, r2 - cb, &k1, &k2);
+                    const double e1 = (double)k1, e2 = (double)k2;
+                    mad = (r1 == r2) ? e1 / 2 : (e1 + e2) / 4;
+                    mad_done = true;
+                }
+                __syncthreads();
+            }
+        }
+    }
     if constexpr (!Traits<T>::is_int) {
         // Bracket from the median histogram.  With B the (monotone) bucket map
         // and N(d) = #{x : |x - med| <= d}, every such x has B(lo) <= B(x) <=
