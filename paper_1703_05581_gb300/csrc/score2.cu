@@ -102,6 +102,14 @@ struct Sh2 {
     float mthr[4];  // MAD bracket: |x - med| <= D1 <=> mthr[0] <= x <= mthr[1]; D2: mthr[2], mthr[3]
     long long mthri[4];  // the same bounds for int profiles
     int mok;
+    // Per-profile FP64 scalars, computed by one thread and broadcast: FP64
+    // issues at a small fraction of the FP32 rate on this part, so a value
+    // every thread needs is never recomputed by every thread.
+    double smed, smad, skmad;  // median, MAD, K * MAD
+    long long s2i;             // int profiles: 2 * median (an integer)
+    float snr_mh, snr_ml, snr_kf;  // float S/N: median as a float pair, fl(K * MAD)
+    int madpos;                // MAD > 0
+    float bw_maxf[16];         // per-width block maxima (float profiles)
     int bin_a, bin_b;
     uint32_t below_a, below_b;
     int phase;
@@ -580,7 +588,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     if (FUSED && m_rows > 1) {
         hrow = prof + (k >> 1) * p0_;
         trow = prof + ((m_rows >> 1) + (k >> 1)) * p0_;
-        sft = (int)(((k + 1) >> 1) % p0_);
+        sft = (int)((uint32_t)((k + 1) >> 1) % (uint32_t)p0);
     } else if (FUSED) {
         hrow = prof;
     } else {
@@ -686,9 +694,9 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
             else sh.cand[i] = fkey(sh.candf[i]);
         }
         __syncthreads();
-        if (cc <= CAPM) {
-            unsigned long long ka, kb;
-            cand_pick2(sh, cc, r1 - mbelow, r2 - mbelow, &ka, &kb);
+        // keys of the two middle order statistics -> the median (one thread)
+        auto put_med = [&](unsigned long long ka, unsigned long long kb) {
+            if (tid != 0) return;
             double a, b;
             if constexpr (Traits<T>::is_int) {
                 a = (double)(int32_t)((uint32_t)ka ^ 0x80000000u);
@@ -697,7 +705,14 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                 a = (double)fkey_inv((uint32_t)ka);
                 b = (double)fkey_inv((uint32_t)kb);
             }
-            med = (r1 == r2) ? a : (a + b) / 2;
+            const double m = (r1 == r2) ? a : (a + b) / 2;
+            sh.smed = m;
+            if constexpr (Traits<T>::is_int) sh.s2i = llrint(2.0 * m);  // a + b: exact
+        };
+        if (cc <= CAPM) {
+            unsigned long long ka, kb;
+            cand_pick2(sh, cc, r1 - mbelow, r2 - mbelow, &ka, &kb);
+            put_med(ka, kb);
         } else {
             const T* vb = buf;
             auto key = [vb](int j) -> uint64_t {
@@ -706,28 +721,20 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
             };
             const uint64_t ka = smem_select64(sh, p0, r1, key);
             const uint64_t kb = (r1 == r2) ? ka : smem_select64(sh, p0, r2, key);
-            double a, b;
-            if constexpr (Traits<T>::is_int) {
-                a = (double)(int32_t)((uint32_t)ka ^ 0x80000000u);
-                b = (double)(int32_t)((uint32_t)kb ^ 0x80000000u);
-            } else {
-                a = (double)fkey_inv((uint32_t)ka);
-                b = (double)fkey_inv((uint32_t)kb);
-            }
-            med = (r1 == r2) ? a : (a + b) / 2;
+            put_med(ka, kb);
         }
         __syncthreads();
+        med = sh.smed;
     }
 
     // ---- MAD (Eq. 3), exact ----
-    double mad = 0.0;
-    bool mad_done = false;
+    bool mad_done = false;  // block-uniform; the MAD itself goes to sh.smad (one thread)
     if constexpr (Traits<T>::is_int) {
         // The same bracket in integers: the deviation is e / 2 with the exact
         // integer e = |2x - s2| (s2 = 2 med), and |2x - s2| <= E exactly when
         // ceil((s2 - E) / 2) <= x <= floor((s2 + E) / 2).
         if (med_hist) {
-            const long long s2 = llrint(2.0 * med);
+            const long long s2 = sh.s2i;
             const long long estep = 1ll << ish;  // half a bucket in units of e
             if (warp < 2) {
                 const int K = NBK;
@@ -818,8 +825,10 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                 if (cc <= CAPM && cb <= r1 && r2 - cb < cc) {
                     unsigned long long k1, k2;
                     cand_pick2(sh, cc, r1 - cb, r2 - cb, &k1, &k2);
-                    const double e1 = (double)k1, e2 = (double)k2;
-                    mad = (r1 == r2) ? e1 / 2 : (e1 + e2) / 4;
+                    if (tid == 0) {
+                        const double e1 = (double)k1, e2 = (double)k2;
+                        sh.smad = (r1 == r2) ? e1 / 2 : (e1 + e2) / 4;
+                    }
                     mad_done = true;
                 }
                 __syncthreads();
@@ -837,13 +846,17 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         // classified exactly by float bounds of med -+ D (directed rounding).
         if (med_hist) {
             if (warp < 2) {  // warp 0 finds D1, warp 1 finds D2
-                const double hstep = 0.5 / (double)inv_m;  // half a bucket
-                const int K = NBK;                         // d up to 4 sigma
+                // The search only chooses D1 and D2 (in FP32; any choice is
+                // correct): the classification below is exact for the chosen
+                // values and the rank check falls back if the band misses.
+                const float hstep = 0.5f / inv_m;  // half a bucket
+                const float medf = __double2float_rn(med);
+                const int K = NBK;                 // d up to 4 sigma
                 auto pb = [&](int b) -> uint32_t { return b >= NBK ? (uint32_t)p0 : sh.hist[b]; };
                 auto lu = [&](int k, uint32_t& L, uint32_t& U) {
-                    const double d = (double)k * hstep;
-                    const int bl = fbucket<NBK>(__double2float_rn(__dsub_rn(med, d)), mean, inv_m);
-                    const int bh = fbucket<NBK>(__double2float_rn(__dadd_rn(med, d)), mean, inv_m);
+                    const float d = (float)k * hstep;
+                    const int bl = fbucket<NBK>(medf - d, mean, inv_m);
+                    const int bh = fbucket<NBK>(medf + d, mean, inv_m);
                     U = pb(bh + 1) - pb(bl);
                     L = bh - 1 >= bl + 1 ? pb(bh) - pb(bl + 1) : 0u;
                 };
@@ -872,7 +885,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                     }) - 1;
                     if (lane == 0) {
                         if (kA >= 0) {
-                            const double d1 = (double)kA * hstep;
+                            const double d1 = (double)((float)kA * hstep);
                             sh.mthr[0] = __double2float_ru(__dsub_ru(med, d1));
                             sh.mthr[1] = __double2float_rd(__dadd_rd(med, d1));
                         } else {
@@ -888,7 +901,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                     });
                     if (lane == 0) {
                         sh.mok = kB <= K;
-                        const double d2 = (double)(kB <= K ? kB : K) * hstep;
+                        const double d2 = (double)((float)(kB <= K ? kB : K) * hstep);
                         sh.mthr[2] = __double2float_ru(__dsub_ru(med, d2));
                         sh.mthr[3] = __double2float_rd(__dadd_rd(med, d2));
                     }
@@ -924,8 +937,10 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                     __syncthreads();
                     unsigned long long k1, k2;
                     cand_pick2(sh, cc, r1 - cb, r2 - cb, &k1, &k2);
-                    const double d1 = dkey_inv(k1), d2 = dkey_inv(k2);
-                    mad = (r1 == r2) ? d1 : (d1 + d2) / 2;
+                    if (tid == 0) {
+                        const double d1 = dkey_inv(k1), d2 = dkey_inv(k2);
+                        sh.smad = (r1 == r2) ? d1 : (d1 + d2) / 2;
+                    }
                     mad_done = true;
                 }
                 __syncthreads();
@@ -941,7 +956,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     __syncthreads();
     if constexpr (Traits<T>::is_int) {
         // e = |2x - (a + b)| is exact; the deviation is e / 2
-        const int s2 = (int)llrint(2.0 * med);
+        const int s2 = (int)sh.s2i;
         int esh = 0;
         const double span = 8.0 * (double)sig / (double)NBK;
         while ((double)(1ll << esh) < span && esh < 40) ++esh;
@@ -979,8 +994,10 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         if (cc <= CAPM) {
             unsigned long long k1, k2;
             cand_pick2(sh, cc, r1 - cbel, r2 - cbel, &k1, &k2);
-            const double e1 = (double)k1, e2 = (double)k2;
-            mad = (r1 == r2) ? e1 / 2 : (e1 + e2) / 4;
+            if (tid == 0) {
+                const double e1 = (double)k1, e2 = (double)k2;
+                sh.smad = (r1 == r2) ? e1 / 2 : (e1 + e2) / 4;
+            }
         } else {
             const T* vb = buf;
             auto key = [vb, s2](int j) -> uint64_t {
@@ -989,7 +1006,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
             };
             const uint64_t e1 = smem_select64(sh, p0, r1, key);
             const uint64_t e2 = (r1 == r2) ? e1 : smem_select64(sh, p0, r2, key);
-            mad = (r1 == r2) ? (double)e1 / 2 : ((double)e1 + (double)e2) / 4;
+            if (tid == 0) sh.smad = (r1 == r2) ? (double)e1 / 2 : ((double)e1 + (double)e2) / 4;
         }
         __syncthreads();
     } else {
@@ -1035,21 +1052,39 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         if (cc <= CAPM && cb <= r1 && r2 - cb < cc) {
             unsigned long long k1, k2;
             cand_pick2(sh, cc, r1 - cb, r2 - cb, &k1, &k2);
-            const double d1 = dkey_inv(k1), d2 = dkey_inv(k2);
-            mad = (r1 == r2) ? d1 : (d1 + d2) / 2;
+            if (tid == 0) {
+                const double d1 = dkey_inv(k1), d2 = dkey_inv(k2);
+                sh.smad = (r1 == r2) ? d1 : (d1 + d2) / 2;
+            }
         } else {
             if (cc <= CAPM) dev_fail(d_status, FFA_ERR_DEVICE);  // bracket invariant broken
             const T* vb = buf;
             auto key = [vb, med](int j) -> uint64_t { return dkey(fabs((double)vb[sidx(j)] - med)); };
             const uint64_t k1 = smem_select64(sh, p0, r1, key);
             const uint64_t k2 = (r1 == r2) ? k1 : smem_select64(sh, p0, r2, key);
-            const double d1 = dkey_inv(k1), d2 = dkey_inv(k2);
-            mad = (r1 == r2) ? d1 : (d1 + d2) / 2;
+            if (tid == 0) {
+                const double d1 = dkey_inv(k1), d2 = dkey_inv(k2);
+                sh.smad = (r1 == r2) ? d1 : (d1 + d2) / 2;
+            }
         }
         __syncthreads();
     }
 
     }  // !mad_done
+
+    // the S/N scalars, once (read after the barriers of the prefix step)
+    if (tid == 0) {
+        const double mad = sh.smad;
+        const double kmad = __dmul_rn(KMAD, mad);
+        sh.madpos = mad > 0.0;
+        sh.skmad = kmad;
+        if constexpr (!Traits<T>::is_int) {
+            const float mh = __double2float_rn(med);
+            sh.snr_mh = mh;
+            sh.snr_ml = __double2float_rn(__dsub_rn(med, (double)mh));
+            sh.snr_kf = __double2float_rn(kmad);
+        }
+    }
 
     // ---- blocked cyclic prefix (bins past p0 repeat the profile) ----
     // Extension blocks (index >= T2) start at bin 32768 > p0, above the value
@@ -1129,10 +1164,13 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     __syncthreads();
     // per-width block maxima: warp w reduces the warp maxima of widths w, w + NW, ...
     for (int wi = warp; wi < wd.n; wi += NW) {
-        double Bw;
-        if constexpr (Traits<T>::is_int) Bw = (double)warp_maxi(lane < NW ? sh.wredi[wi][lane] : INT32_MIN);
-        else Bw = (double)warp_max(lane < NW ? sh.wred[wi][lane] : -INFINITY);
-        if (lane == 0) sh.bw_max[wi] = Bw;
+        if constexpr (Traits<T>::is_int) {
+            const double Bw = (double)warp_maxi(lane < NW ? sh.wredi[wi][lane] : INT32_MIN);
+            if (lane == 0) sh.bw_max[wi] = Bw;
+        } else {
+            const float bf = warp_max(lane < NW ? sh.wred[wi][lane] : -INFINITY);
+            if (lane == 0) sh.bw_maxf[wi] = bf;
+        }
     }
     __syncthreads();
     // S/N_w = (B_w - w*med) / (K*MAD*sqrt(w)).  sqrt(w) for w = 2^n is
@@ -1145,7 +1183,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     // the FP64 quotient (GB300's FP64 rate is a small fraction of FP32's).
     // Ties go to the smaller width.
     if (warp == 0) {
-        const double kmad = __dmul_rn(KMAD, mad);
+        const double kmad = sh.skmad;
         constexpr double SQRT2 = 1.4142135623730951;  // sqrt(2) rounded to nearest
         float key = -INFINITY;
         if constexpr (Traits<T>::is_int) {
@@ -1158,17 +1196,17 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                 key = __double2float_rn(num) * rs;
             }
         } else {
-            const float mh = __double2float_rn(med);
-            const float ml = __double2float_rn(__dsub_rn(med, (double)mh));
-            const float kf = __double2float_rn(kmad);
+            const float mh = sh.snr_mh, ml = sh.snr_ml, kf = sh.snr_kf;
             if (lane < wd.n) {
                 const float w = (float)wd.w[lane];
-                const float bx = (float)sh.bw_max[lane];
+                const float bx = sh.bw_maxf[lane];
                 float hi, lo;
                 two_sum(bx, -(w * mh), hi, lo);  // w * mh, w * ml exact (w a power of two)
                 const float num = __fadd_rn(hi, __fsub_rn(lo, w * ml));
                 const int n = __ffs(wd.w[lane]) - 1;
-                const float sq = (n & 1) ? (float)ldexp(SQRT2, (n - 1) / 2) : ldexpf(1.0f, n / 2);
+                // fl(sqrt 2) * 2^((n-1)/2) is exactly fl(sqrt(2) * 2^((n-1)/2))
+                constexpr float SQRT2F = (float)SQRT2;
+                const float sq = (n & 1) ? ldexpf(SQRT2F, (n - 1) / 2) : ldexpf(1.0f, n / 2);
                 key = __fdiv_rn(num, __fmul_rn(kf, sq));
             }
         }
@@ -1187,33 +1225,34 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                 const double w = (double)wd.w[bw];
                 const double num = __dsub_rn(sh.bw_max[bw], __dmul_rn(w, med));
                 const double sq = (n & 1) ? ldexp(SQRT2, (n - 1) / 2) : ldexp(1.0, n / 2);
-                sh.dred[0] = __ddiv_rn(num, __dmul_rn(kmad, sq));
+                sh.fred[0] = __double2float_rn(__ddiv_rn(num, __dmul_rn(kmad, sq)));
             } else {
-                sh.dred[0] = (double)key;
+                sh.fred[0] = key;
             }
             sh.ired[0] = bw;
         }
     }
     __syncthreads();
-    const double bestv = sh.dred[0];
+    const float bestv = sh.fred[0];
     const int bw = sh.ired[0];
+    const int madpos = sh.madpos;
     __syncthreads();
     // first argmax of the winning width, recomputed bit-identically
     T target;
     if constexpr (Traits<T>::is_int) target = (T)warp_maxi(lane < NW ? sh.wredi[bw][lane] : INT32_MIN);
     else target = (T)warp_max(lane < NW ? sh.wred[bw][lane] : -INFINITY);
     int first = -1;
-    if (own && mad > 0.0) (void)width_max<T, true>(x, sh, buf, tid, wd.w[bw], nvalid, target, &first);
+    if (own && madpos) (void)width_max<T, true>(x, sh, buf, tid, wd.w[bw], nvalid, target, &first);
     const int pos = blk_mini(first >= 0 ? base_pos + first : 0x7fffffff, sh);
     if (tid == 0) {
         ffa_record out;
-        if (!(mad > 0.0)) {
+        if (!madpos) {
             out.snr = 0.0f;
             out.width = wd.w[0];
             out.phase = 0;
             out.flags = 1;
         } else {
-            out.snr = __double2float_rn(bestv);
+            out.snr = bestv;
             out.width = wd.w[bw];
             out.phase = pos == 0x7fffffff ? 0 : pos;
             out.flags = 0;
