@@ -105,8 +105,7 @@ struct Sh2 {
     // Per-profile FP64 scalars, computed by one thread and broadcast: FP64
     // issues at a small fraction of the FP32 rate on this part, so a value
     // every thread needs is never recomputed by every thread.
-    double smed, smad, skmad;  // median, MAD, K * MAD
-    long long s2i;             // int profiles: 2 * median (an integer)
+    double smed, skmad;        // median, K * MAD
     float snr_mh, snr_ml, snr_kf;  // float S/N: median as a float pair, fl(K * MAD)
     int madpos;                // MAD > 0
     float bw_maxf[16];         // per-width block maxima (float profiles)
@@ -120,18 +119,16 @@ __device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+// Warp maxima in one instruction (redux.sync; the .f32 form is new with the
+// sm_100 family).  Inputs here are never NaN; -0 and +0 compare equal in
+// every use of the result.
 __device__ __forceinline__ float warp_max(float v) {
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
 }
-__device__ __forceinline__ int warp_maxi(int v) {
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ int warp_mini(int v) {
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
+__device__ __forceinline__ int warp_maxi(int v) { return __reduce_max_sync(0xffffffffu, v); }
+__device__ __forceinline__ int warp_mini(int v) { return __reduce_min_sync(0xffffffffu, v); }
 
 // block sums of a and b and the max of c (one barrier pair)
 template <class C>
@@ -151,6 +148,29 @@ __device__ void blk_stats(float& a, float& b, float& c, Sh2<C>& sh) {
     b = warp_sum(l < NW ? sh.wred[0][l] : 0.0f);
     c = warp_max(l < NW ? sh.wred[1][l] : 0.0f);
     __syncthreads();
+}
+// The same statistics split around a barrier the caller already has: warp
+// partials before it, the block values after it (the partials' slots are
+// not written again before the caller's next barrier).
+template <class C>
+__device__ __forceinline__ void blk_stats_part(float a, float b, float c, Sh2<C>& sh) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_max(c);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sh.fred[w] = a;
+        sh.wred[0][w] = b;
+        sh.wred[1][w] = c;
+    }
+}
+template <class C>
+__device__ __forceinline__ void blk_stats_fin(float& a, float& b, float& c, const Sh2<C>& sh) {
+    FFA_CFG_ALIASES
+    const int l = threadIdx.x & 31;
+    a = warp_sum(l < NW ? sh.fred[l] : 0.0f);
+    b = warp_sum(l < NW ? sh.wred[0][l] : 0.0f);
+    c = warp_max(l < NW ? sh.wred[1][l] : 0.0f);
 }
 template <class C>
 __device__ int blk_mini(int v, Sh2<C>& sh) {
@@ -594,19 +614,36 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     } else {
         hrow = prof + k * p0_;
     }
+    // the sum, sum of squares and largest |x| (they only scale the median's
+    // buckets) accumulate as the profile is loaded
+    float fs = 0.0f, fq = 0.0f, famax = 0.0f;
+    auto acc = [&](T v) {
+        const float f = (float)v;
+        fs += f;
+        fq = fmaf(f, f, fq);
+        famax = fmaxf(famax, fabsf(f));
+    };
     if (trow) {
         // the tail row read from column sft on: two contiguous runs
         const int n1 = p0 - sft;
 #pragma unroll 4
         for (int j = tid; j < p0; j += T2) {
             const T t = j < n1 ? trow[j + sft] : trow[j - n1];
-            buf[sidx(j)] = hrow[j] + t;
+            const T v = hrow[j] + t;
+            buf[sidx(j)] = v;
+            acc(v);
         }
     } else {
 #pragma unroll 4
-        for (int j = tid; j < p0; j += T2) buf[sidx(j)] = hrow[j];
+        for (int j = tid; j < p0; j += T2) {
+            const T v = hrow[j];
+            buf[sidx(j)] = v;
+            acc(v);
+        }
     }
+    blk_stats_part(fs, fq, famax, sh);
     __syncthreads();
+    blk_stats_fin(fs, fq, famax, sh);
     T x[R2];
     const int base_pos = tid * R2;
     int nvalid = p0 - base_pos;
@@ -624,18 +661,6 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
 
     // ---- median (Eq. 3), exact ----
     const uint32_t r1 = (uint32_t)((p0 - 1) / 2), r2 = (uint32_t)(p0 / 2);
-    float fs = 0.0f, fq = 0.0f, famax = 0.0f;
-    if (nvalid > 0) {
-#pragma unroll
-        for (int r = 0; r < R2; ++r)
-            if (r < nvalid) {
-                float v = (float)x[r];
-                fs += v;
-                fq = fmaf(v, v, fq);
-                famax = fmaxf(famax, fabsf(v));
-            }
-    }
-    blk_stats(fs, fq, famax, sh);
     const float mean = fs / (float)p0;
     const float msq = fq / (float)p0;
     const float amax = famax;
@@ -684,7 +709,26 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
             }
     }
     __syncthreads();
-    double med;
+    // The two middle order statistics come out as keys (mka, mkb) in every
+    // thread.  Every thread decodes what it needs without FP64: 2 * median
+    // for int profiles (exact), fl(median) for float ones (it only guides the
+    // MAD search).  The exact FP64 median is formed once (med_of), by the
+    // last thread while the first warps search, and read from sh.smed after
+    // the next barrier.
+    unsigned long long mka = 0, mkb = 0;
+    long long s2m = 0;  // int profiles: 2 * median
+    float medf = 0.0f;  // float profiles: fl(median)
+    auto med_of = [&]() -> double {
+        double a, b;
+        if constexpr (Traits<T>::is_int) {
+            a = (double)(int32_t)((uint32_t)mka ^ 0x80000000u);
+            b = (double)(int32_t)((uint32_t)mkb ^ 0x80000000u);
+        } else {
+            a = (double)fkey_inv((uint32_t)mka);
+            b = (double)fkey_inv((uint32_t)mkb);
+        }
+        return (r1 == r2) ? a : (a + b) / 2;
+    };
     bool med_hist;  // the median came from the histogram (its prefix counts are in hist)
     {
         const uint32_t cc = sh.cnt;
@@ -694,47 +738,42 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
             else sh.cand[i] = fkey(sh.candf[i]);
         }
         __syncthreads();
-        // keys of the two middle order statistics -> the median (one thread)
-        auto put_med = [&](unsigned long long ka, unsigned long long kb) {
-            if (tid != 0) return;
-            double a, b;
-            if constexpr (Traits<T>::is_int) {
-                a = (double)(int32_t)((uint32_t)ka ^ 0x80000000u);
-                b = (double)(int32_t)((uint32_t)kb ^ 0x80000000u);
-            } else {
-                a = (double)fkey_inv((uint32_t)ka);
-                b = (double)fkey_inv((uint32_t)kb);
-            }
-            const double m = (r1 == r2) ? a : (a + b) / 2;
-            sh.smed = m;
-            if constexpr (Traits<T>::is_int) sh.s2i = llrint(2.0 * m);  // a + b: exact
-        };
         if (cc <= CAPM) {
-            unsigned long long ka, kb;
-            cand_pick2(sh, cc, r1 - mbelow, r2 - mbelow, &ka, &kb);
-            put_med(ka, kb);
+            cand_pick2(sh, cc, r1 - mbelow, r2 - mbelow, &mka, &mkb);
         } else {
             const T* vb = buf;
             auto key = [vb](int j) -> uint64_t {
                 if constexpr (Traits<T>::is_int) return (uint64_t)ikey((int32_t)vb[sidx(j)]);
                 else return (uint64_t)fkey((float)vb[sidx(j)]);
             };
-            const uint64_t ka = smem_select64(sh, p0, r1, key);
-            const uint64_t kb = (r1 == r2) ? ka : smem_select64(sh, p0, r2, key);
-            put_med(ka, kb);
+            mka = smem_select64(sh, p0, r1, key);
+            mkb = (r1 == r2) ? mka : smem_select64(sh, p0, r2, key);
+        }
+        if constexpr (Traits<T>::is_int) {
+            const long long a = (int32_t)((uint32_t)mka ^ 0x80000000u);
+            const long long b = (int32_t)((uint32_t)mkb ^ 0x80000000u);
+            s2m = (r1 == r2) ? 2 * a : a + b;
+        } else {
+            const float a = fkey_inv((uint32_t)mka), b = fkey_inv((uint32_t)mkb);
+            medf = (r1 == r2) ? a : __fmul_rn(__fadd_rn(a, b), 0.5f);
         }
         __syncthreads();
-        med = sh.smed;
+        if (tid == T2 - 1) sh.smed = med_of();
     }
 
     // ---- MAD (Eq. 3), exact ----
-    bool mad_done = false;  // block-uniform; the MAD itself goes to sh.smad (one thread)
+    // The two order statistics of the deviations come out as keys (mk1, mk2)
+    // in every thread: exact integers e = |2x - 2 med| for int profiles,
+    // FP64 keys (dkey) of |x - med| for float ones; the MAD itself is formed
+    // once, with the S/N factors, before the widths.
+    bool mad_done = false;  // block-uniform
+    unsigned long long mk1 = 0, mk2 = 0;
     if constexpr (Traits<T>::is_int) {
         // The same bracket in integers: the deviation is e / 2 with the exact
         // integer e = |2x - s2| (s2 = 2 med), and |2x - s2| <= E exactly when
         // ceil((s2 - E) / 2) <= x <= floor((s2 + E) / 2).
         if (med_hist) {
-            const long long s2 = sh.s2i;
+            const long long s2 = s2m;
             const long long estep = 1ll << ish;  // half a bucket in units of e
             if (warp < 2) {
                 const int K = NBK;
@@ -823,12 +862,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                 __syncthreads();
                 const uint32_t cc = sh.cnt, cb = sh.below;
                 if (cc <= CAPM && cb <= r1 && r2 - cb < cc) {
-                    unsigned long long k1, k2;
-                    cand_pick2(sh, cc, r1 - cb, r2 - cb, &k1, &k2);
-                    if (tid == 0) {
-                        const double e1 = (double)k1, e2 = (double)k2;
-                        sh.smad = (r1 == r2) ? e1 / 2 : (e1 + e2) / 4;
-                    }
+                    cand_pick2(sh, cc, r1 - cb, r2 - cb, &mk1, &mk2);
                     mad_done = true;
                 }
                 __syncthreads();
@@ -850,7 +884,6 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                 // correct): the classification below is exact for the chosen
                 // values and the rank check falls back if the band misses.
                 const float hstep = 0.5f / inv_m;  // half a bucket
-                const float medf = __double2float_rn(med);
                 const int K = NBK;                 // d up to 4 sigma
                 auto pb = [&](int b) -> uint32_t { return b >= NBK ? (uint32_t)p0 : sh.hist[b]; };
                 auto lu = [&](int k, uint32_t& L, uint32_t& U) {
@@ -885,6 +918,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                     }) - 1;
                     if (lane == 0) {
                         if (kA >= 0) {
+                            const double med = med_of();
                             const double d1 = (double)((float)kA * hstep);
                             sh.mthr[0] = __double2float_ru(__dsub_ru(med, d1));
                             sh.mthr[1] = __double2float_rd(__dadd_rd(med, d1));
@@ -901,6 +935,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                     });
                     if (lane == 0) {
                         sh.mok = kB <= K;
+                        const double med = med_of();
                         const double d2 = (double)((float)(kB <= K ? kB : K) * hstep);
                         sh.mthr[2] = __double2float_ru(__dsub_ru(med, d2));
                         sh.mthr[3] = __double2float_rd(__dadd_rd(med, d2));
@@ -933,14 +968,10 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                 __syncthreads();
                 const uint32_t cc = sh.cnt, cb = sh.below;
                 if (cc <= CAPM && cb <= r1 && r2 - cb < cc) {
+                    const double med = sh.smed;
                     for (uint32_t i = tid; i < cc; i += T2) sh.cand[i] = dkey(fabs((double)sh.candf[i] - med));
                     __syncthreads();
-                    unsigned long long k1, k2;
-                    cand_pick2(sh, cc, r1 - cb, r2 - cb, &k1, &k2);
-                    if (tid == 0) {
-                        const double d1 = dkey_inv(k1), d2 = dkey_inv(k2);
-                        sh.smad = (r1 == r2) ? d1 : (d1 + d2) / 2;
-                    }
+                    cand_pick2(sh, cc, r1 - cb, r2 - cb, &mk1, &mk2);
                     mad_done = true;
                 }
                 __syncthreads();
@@ -954,9 +985,10 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         sh.below = 0;
     }
     __syncthreads();
+    const double med = sh.smed;  // written before this barrier
     if constexpr (Traits<T>::is_int) {
         // e = |2x - (a + b)| is exact; the deviation is e / 2
-        const int s2 = (int)sh.s2i;
+        const int s2 = (int)s2m;
         int esh = 0;
         const double span = 8.0 * (double)sig / (double)NBK;
         while ((double)(1ll << esh) < span && esh < 40) ++esh;
@@ -992,21 +1024,15 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         __syncthreads();
         const uint32_t cc = sh.cnt;
         if (cc <= CAPM) {
-            unsigned long long k1, k2;
-            cand_pick2(sh, cc, r1 - cbel, r2 - cbel, &k1, &k2);
-            if (tid == 0) {
-                const double e1 = (double)k1, e2 = (double)k2;
-                sh.smad = (r1 == r2) ? e1 / 2 : (e1 + e2) / 4;
-            }
+            cand_pick2(sh, cc, r1 - cbel, r2 - cbel, &mk1, &mk2);
         } else {
             const T* vb = buf;
             auto key = [vb, s2](int j) -> uint64_t {
                 const int e = 2 * (int)vb[sidx(j)] - s2;
                 return (uint64_t)(uint32_t)(e < 0 ? -e : e);
             };
-            const uint64_t e1 = smem_select64(sh, p0, r1, key);
-            const uint64_t e2 = (r1 == r2) ? e1 : smem_select64(sh, p0, r2, key);
-            if (tid == 0) sh.smad = (r1 == r2) ? (double)e1 / 2 : ((double)e1 + (double)e2) / 4;
+            mk1 = smem_select64(sh, p0, r1, key);
+            mk2 = (r1 == r2) ? mk1 : smem_select64(sh, p0, r2, key);
         }
         __syncthreads();
     } else {
@@ -1050,41 +1076,18 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         for (uint32_t i = tid; i < cc && i < CAPM; i += T2) sh.cand[i] = dkey(fabs((double)sh.candf[i] - med));
         __syncthreads();
         if (cc <= CAPM && cb <= r1 && r2 - cb < cc) {
-            unsigned long long k1, k2;
-            cand_pick2(sh, cc, r1 - cb, r2 - cb, &k1, &k2);
-            if (tid == 0) {
-                const double d1 = dkey_inv(k1), d2 = dkey_inv(k2);
-                sh.smad = (r1 == r2) ? d1 : (d1 + d2) / 2;
-            }
+            cand_pick2(sh, cc, r1 - cb, r2 - cb, &mk1, &mk2);
         } else {
             if (cc <= CAPM) dev_fail(d_status, FFA_ERR_DEVICE);  // bracket invariant broken
             const T* vb = buf;
             auto key = [vb, med](int j) -> uint64_t { return dkey(fabs((double)vb[sidx(j)] - med)); };
-            const uint64_t k1 = smem_select64(sh, p0, r1, key);
-            const uint64_t k2 = (r1 == r2) ? k1 : smem_select64(sh, p0, r2, key);
-            if (tid == 0) {
-                const double d1 = dkey_inv(k1), d2 = dkey_inv(k2);
-                sh.smad = (r1 == r2) ? d1 : (d1 + d2) / 2;
-            }
+            mk1 = smem_select64(sh, p0, r1, key);
+            mk2 = (r1 == r2) ? mk1 : smem_select64(sh, p0, r2, key);
         }
         __syncthreads();
     }
 
     }  // !mad_done
-
-    // the S/N scalars, once (read after the barriers of the prefix step)
-    if (tid == 0) {
-        const double mad = sh.smad;
-        const double kmad = __dmul_rn(KMAD, mad);
-        sh.madpos = mad > 0.0;
-        sh.skmad = kmad;
-        if constexpr (!Traits<T>::is_int) {
-            const float mh = __double2float_rn(med);
-            sh.snr_mh = mh;
-            sh.snr_ml = __double2float_rn(__dsub_rn(med, (double)mh));
-            sh.snr_kf = __double2float_rn(kmad);
-        }
-    }
 
     // ---- blocked cyclic prefix (bins past p0 repeat the profile) ----
     // Extension blocks (index >= T2) start at bin 32768 > p0, above the value
@@ -1147,6 +1150,30 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     }
     __syncthreads();
 
+    // The MAD and the S/N factors, once, by the last thread (usually one
+    // without bins, so the FP64 latency hides behind the widths); read after
+    // the barrier that ends the widths.
+    if (tid == T2 - 1) {
+        const double med = sh.smed;
+        double mad;
+        if constexpr (Traits<T>::is_int) {
+            const double e1 = (double)mk1, e2 = (double)mk2;  // exact integers
+            mad = (r1 == r2) ? e1 / 2 : (e1 + e2) / 4;
+        } else {
+            const double d1 = dkey_inv(mk1), d2 = dkey_inv(mk2);
+            mad = (r1 == r2) ? d1 : (d1 + d2) / 2;
+        }
+        const double kmad = __dmul_rn(KMAD, mad);
+        sh.madpos = mad > 0.0;
+        sh.skmad = kmad;
+        if constexpr (!Traits<T>::is_int) {
+            const float mh = __double2float_rn(med);
+            sh.snr_mh = mh;
+            sh.snr_ml = __double2float_rn(__dsub_rn(med, (double)mh));
+            sh.snr_kf = __double2float_rn(kmad);
+        }
+    }
+
     // ---- widths (Section 2.2.1): per-thread maxima, warp-reduced ----
     const bool own = base_pos < p0;
     int dummy = -1;
@@ -1183,7 +1210,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     // the FP64 quotient (GB300's FP64 rate is a small fraction of FP32's).
     // Ties go to the smaller width.
     if (warp == 0) {
-        const double kmad = sh.skmad;
+        const double kmad = sh.skmad, med = sh.smed;
         constexpr double SQRT2 = 1.4142135623730951;  // sqrt(2) rounded to nearest
         float key = -INFINITY;
         if constexpr (Traits<T>::is_int) {
