@@ -310,17 +310,21 @@ __device__ void blk_find(Sh2<C>& sh, uint32_t rank, int* bin, uint32_t* below) {
 
 // Keys of ranks ta <= tb among the keys sh.cand[0..n) (ties broken by index):
 // the n x n integer comparisons are spread over the whole CTA and each
-// candidate's rank is accumulated in shared memory (sh.hist is free here).
-// Integer keys, not doubles: FP64 compares are slow on this part.
-template <class C>
+// candidate's rank is accumulated in shared memory.  Integer keys, not
+// doubles: FP64 compares are slow on this part.  The rank counters live in
+// ired2 (the int gather buffer, already turned into keys), so the median
+// histogram stays intact for the MAD bracket; ZEROED: the caller cleared
+// counters 0..n) before its last barrier.  Every caller passes a barrier
+// before it writes cand, ired2 or ukey again.
+template <bool ZEROED = false, class C>
 __device__ void cand_pick2(Sh2<C>& sh, uint32_t n, uint32_t ta, uint32_t tb, unsigned long long* ka,
                            unsigned long long* kb) {
     FFA_CFG_ALIASES
-    // rank counters in ired2 (the int gather buffer, already turned into keys):
-    // the median histogram stays intact for the MAD bracket
     uint32_t* rank = reinterpret_cast<uint32_t*>(sh.ired2);
-    for (uint32_t i = threadIdx.x; i < n; i += T2) rank[i] = 0;
-    __syncthreads();
+    if (!ZEROED) {
+        for (uint32_t i = threadIdx.x; i < n; i += T2) rank[i] = 0;
+        __syncthreads();
+    }
     const uint32_t chunks = (T2 + n - 1) / (n ? n : 1);  // threads per candidate
     const uint32_t pairs = n * chunks;
     for (uint32_t p = threadIdx.x; p < pairs; p += T2) {
@@ -342,7 +346,6 @@ __device__ void cand_pick2(Sh2<C>& sh, uint32_t n, uint32_t ta, uint32_t tb, uns
     __syncthreads();
     *ka = sh.ukey[0];
     *kb = sh.ukey[1];
-    __syncthreads();
 }
 
 // Exact rank-`rank` 64-bit key of keyf(j), j < n, by an 8-pass radix select
@@ -736,10 +739,11 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         for (uint32_t i = tid; i < cc && i < CAPM; i += T2) {
             if constexpr (Traits<T>::is_int) sh.cand[i] = ikey(sh.ired2[i]);
             else sh.cand[i] = fkey(sh.candf[i]);
+            reinterpret_cast<uint32_t*>(sh.ired2)[i] = 0;  // rank counter (value read above)
         }
         __syncthreads();
         if (cc <= CAPM) {
-            cand_pick2(sh, cc, r1 - mbelow, r2 - mbelow, &mka, &mkb);
+            cand_pick2<true>(sh, cc, r1 - mbelow, r2 - mbelow, &mka, &mkb);
         } else {
             const T* vb = buf;
             auto key = [vb](int j) -> uint64_t {
@@ -969,9 +973,12 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
                 const uint32_t cc = sh.cnt, cb = sh.below;
                 if (cc <= CAPM && cb <= r1 && r2 - cb < cc) {
                     const double med = sh.smed;
-                    for (uint32_t i = tid; i < cc; i += T2) sh.cand[i] = dkey(fabs((double)sh.candf[i] - med));
+                    for (uint32_t i = tid; i < cc; i += T2) {
+                        sh.cand[i] = dkey(fabs((double)sh.candf[i] - med));
+                        reinterpret_cast<uint32_t*>(sh.ired2)[i] = 0;  // rank counter
+                    }
                     __syncthreads();
-                    cand_pick2(sh, cc, r1 - cb, r2 - cb, &mk1, &mk2);
+                    cand_pick2<true>(sh, cc, r1 - cb, r2 - cb, &mk1, &mk2);
                     mad_done = true;
                 }
                 __syncthreads();
