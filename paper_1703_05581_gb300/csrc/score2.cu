@@ -1182,11 +1182,17 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     }
 
     // ---- widths (Section 2.2.1): per-thread maxima, warp-reduced ----
+    // Every thread with profile bins scores all R bins of its block: in the
+    // one block that runs past p0 the extra boxes start at bins p0 + i and
+    // are the cyclic boxes at bin i again (from the extended prefix), so the
+    // maxima are unchanged up to rounding (exactly, for int profiles) and no
+    // per-bin bound check is needed.  A first argmax found there is reported
+    // at bin i (i mod p0 for profiles shorter than a block).
     const bool own = base_pos < p0;
     int dummy = -1;
     for (int wi = 0; wi < wd.n; ++wi) {
         T m = B::lowest();
-        if (own) m = width_max<T, false>(x, sh, buf, tid, wd.w[wi], nvalid, (T)0, &dummy);
+        if (own) m = width_max<T, false>(x, sh, buf, tid, wd.w[wi], R2, (T)0, &dummy);
         if constexpr (Traits<T>::is_int) {
             m = warp_maxi(m);
             if (lane == 0) sh.wredi[wi][warp] = m;
@@ -1276,8 +1282,13 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     if constexpr (Traits<T>::is_int) target = (T)warp_maxi(lane < NW ? sh.wredi[bw][lane] : INT32_MIN);
     else target = (T)warp_max(lane < NW ? sh.wred[bw][lane] : -INFINITY);
     int first = -1;
-    if (own && madpos) (void)width_max<T, true>(x, sh, buf, tid, wd.w[bw], nvalid, target, &first);
-    const int pos = blk_mini(first >= 0 ? base_pos + first : 0x7fffffff, sh);
+    if (own && madpos) (void)width_max<T, true>(x, sh, buf, tid, wd.w[bw], R2, target, &first);
+    int fpos = 0x7fffffff;
+    if (first >= 0) {
+        fpos = base_pos + first;
+        if (fpos >= p0) fpos %= p0;  // a box of the wrapped tail (p0 < R wraps more than once)
+    }
+    const int pos = blk_mini(fpos, sh);
     if (tid == 0) {
         ffa_record out;
         if (!madpos) {
