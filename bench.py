@@ -96,8 +96,8 @@ ALU_LANES = 152 * 128
 ALU_MAX_MHZ = 2070.0
 # DRAM bytes per profile bin of one k_score2 launch (read + write), from the
 # ncu capture summarised in profiles/k_score2_p0_20000_m4096.md:
-# (329.27 MB + 11.71 MB) / (4096 * 20000).  Set to None when the kernel changes.
-SCORE_DRAM_BYTES_PER_ELEM = (329600512 + 11606528) / (4096 * 20000)
+# (329.25 MB + 11.89 MB) / (4096 * 20000).  Set to None when the kernel changes.
+SCORE_DRAM_BYTES_PER_ELEM = (329247232 + 11889920) / (4096 * 20000)
 
 
 def score_ops(entries) -> np.ndarray:
