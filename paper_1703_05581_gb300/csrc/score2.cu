@@ -14,13 +14,18 @@
 // value, rounded, clamped) feeds a shared-memory histogram; the
 // bucket(s) holding the wanted ranks are gathered and ranked, which gives the
 // exact order statistics because a monotone bucket map preserves order
-// between buckets.  For float profiles the deviations |x - med| are bucketed
-// from their FP32 values |x - fl(med)|, which differ from the exact FP64
-// deviations by at most E = max|x| * 2^-20; gathering one extra bucket on each
-// side (more when E is large against a bucket) catches every sample whose
-// exact deviation can be the MAD, and those few are re-evaluated in FP64.
-// If a gather overflows its buffer, an exact radix select over the register
-// values takes over.
+// between buckets.  The MAD reuses that histogram: its prefix counts bound
+// how many samples lie within d of the median, so two warps bracket the MAD
+// between D1 and D2 and only the samples with D1 < |x - med| <= D2
+// (classified exactly, by float bounds of med -+ D taken with directed
+// rounding) are gathered and ranked by their exact deviations.  If the band
+// misses the wanted ranks, a histogram of the FP32 deviations |x - fl(med)|
+// (within E = max|x| * 2^-20 of the exact ones, so one extra bucket on each
+// side catches every candidate) takes over; if a gather overflows its
+// buffer, an exact radix select over the profile in shared memory does.
+// The order statistics travel as integer keys held by every thread; each
+// FP64 value of a profile (median, MAD, the S/N factors) is formed once by
+// one thread and shared, as FP64 issues at a small fraction of the FP32 rate.
 //
 // Box sums.  With the in-block exclusive prefix c_t[o] (FP32) and the block
 // offsets Cb[t] = sum of earlier blocks (float-float), the cyclic box sum of
@@ -30,7 +35,9 @@
 // thread's own prefix and the next block's.  Int profiles use the same
 // formulas in wrapping int32 arithmetic, which is exact for box sums below
 // 2^31.  Only the maximum of each width is kept; the winning width's first
-// argmax is found afterwards by recomputing that width, bit-identically.
+// argmax is found afterwards by recomputing that width, bit-identically.  The
+// block that runs past p0 scores all its bins: its extra boxes are cyclic
+// boxes of the first bins again, so no per-bin bound check is needed.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
