@@ -40,13 +40,20 @@
 //   R14 a base period with fewer than min_rows data rows is skipped;
 //   R15 Algorithm 2 filters first: b_w[j] = sum_{i<w} x[(j+i) mod p0], not
 //      normalised; I_max = its maximum (first position j* on ties);
-//   R16 the Algorithm 2 exclusion window is the 2h+1 filtered bins within
-//      cyclic distance h = floor(excl_frac * p0 / 2) of j* (excl_frac 0.2:
-//      "20 % of the profile width"); I_av and sigma are the mean and the
-//      population standard deviation of the other filtered bins (two-pass);
-//   R17 A_w = (I_max - I_av) / sigma, score = max over widths with the R13
-//      tie-breaks; sigma = 0 or fewer than 2 off-window bins gives score 0
-//      and flag bit 0.
+//   R16 the Algorithm 2 exclusion window ("20 % of the profile width",
+//      centred on the position of I_max) is the 2h+1 profile bins within
+//      cyclic distance h = floor(excl_frac * p0 / 2) of the box's centre
+//      c = (j* + floor(w/2)) mod p0; I_av and sigma are the FP64 mean and
+//      population standard deviation (two-pass) of the other, unfiltered,
+//      profile bins ("the average value and standard deviation of the
+//      profile ... based on the remaining 80 %");
+//   R17 the matched filter keeps unit noise by dividing by sqrt(w), as in
+//      Algorithm 1, so with the off-pulse level scaled the same way
+//      A_w = (I_max - w I_av) / (sigma sqrt(w)); score = max over widths with
+//      the R13 tie-breaks; sigma = 0 or fewer than 2 off-window bins gives
+//      score 0 and flag bit 0.  (Reading the statistics off the filtered
+//      bins instead puts white noise's 5 sigma_gauss at S/N 12.2, against
+//      the 7.1 printed in Section 4.3; this reading gives about 7.)
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -415,10 +422,11 @@ void oracle_score_alg1_i64(const int64_t* x, int64_t p0, const int32_t* widths, 
 }
 
 // --- Section 2.2.2 Algorithm 2 ---------------------------------------------
-// Boxcar filter first (R15), then the maximum, an exclusion window of about
-// excl_frac of the profile around it (R16), and the S/N against the mean and
-// standard deviation of the rest (Eq. 5, R17).  median/mad of the record are
-// set to I_av and sigma of the winning width.
+// Boxcar filter first (R15), then per width the maximum I_max at j*, an
+// exclusion window of about excl_frac of the profile centred on that box
+// (R16), and the S/N of Eq. 5 against the mean and standard deviation of the
+// remaining profile bins (R17).  median/mad of the record are set to I_av and
+// sigma of the winning width.
 void oracle_score_alg2_f64(const double* x, int64_t p0, const int32_t* widths, int32_t nw,
                            double excl_frac, oracle_score* out) {
     int64_t wmax = 0;
@@ -432,31 +440,34 @@ void oracle_score_alg2_f64(const double* x, int64_t p0, const int32_t* widths, i
     int32_t best_w = widths[0], best_j = 0;
     double best_av = 0.0, best_sd = 0.0;
     bool any = false;
-    std::vector<double> b((size_t)p0);
     for (int32_t t = 0; t < nw; ++t) {
         const int64_t w = widths[t];
         int64_t jmax = 0;
-        for (int64_t j = 0; j < p0; ++j) {
-            b[j] = c[j + w] - c[j];
-            if (b[j] > b[jmax]) jmax = j;
+        double bmax = c[w] - c[0];
+        for (int64_t j = 1; j < p0; ++j) {
+            const double b = c[j + w] - c[j];
+            if (b > bmax) {
+                bmax = b;
+                jmax = j;
+            }
         }
         if (n_off < 2) continue;
+        const int64_t centre = (jmax + w / 2) % p0;
         auto off = [&](int64_t j) {
-            int64_t d = j - jmax;
-            d = ((d % p0) + p0) % p0;  // cyclic distance from jmax
+            int64_t d = ((j - centre) % p0 + p0) % p0;  // cyclic distance from the centre
             d = std::min(d, p0 - d);
             return d > h;
         };
         double sum = 0.0;
         for (int64_t j = 0; j < p0; ++j)
-            if (off(j)) sum += b[j];
+            if (off(j)) sum += x[j];
         const double av = sum / (double)n_off;
         double ss = 0.0;
         for (int64_t j = 0; j < p0; ++j)
-            if (off(j)) ss += (b[j] - av) * (b[j] - av);
+            if (off(j)) ss += (x[j] - av) * (x[j] - av);
         const double sd = std::sqrt(ss / (double)n_off);
         if (!(sd > 0.0)) continue;
-        const double a = (b[jmax] - av) / sd;
+        const double a = (bmax - (double)w * av) / (sd * std::sqrt((double)w));
         any = true;
         if (a > best) {
             best = a;

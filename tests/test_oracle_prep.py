@@ -96,3 +96,63 @@ def test_quantise_half_to_even(orc):
 def test_constant_series_degenerate(orc):
     z64, z32, q, mean, std, deg = orc.normalise(np.full(100, 5.0))
     assert deg and std == 0.0 and not z32.any() and not q.any()
+
+
+def _numpy_octaves(x, d0, w, n_oct):
+    """Section 2.3's per-octave preparation written out with numpy: the raw
+    series is pre-downsampled by D0, then octave o sums adjacent pairs of the
+    previous octave's *raw* series, takes its running median with the same
+    window W in current samples (W doubles in initial samples), subtracts it
+    and normalises by the population mean and standard deviation."""
+    n0 = x.size // d0
+    raw = x[: n0 * d0].astype(np.float64).reshape(n0, d0).sum(axis=1)
+    out = []
+    for o in range(n_oct):
+        if o > 0:
+            m = raw.size // 2
+            raw = raw[0:2 * m:2] + raw[1:2 * m:2]
+        r = raw - brute_runmed(raw, w)
+        out.append((r - r.mean()) / r.std())
+    return out
+
+
+def test_octave_chain_matches_numpy(orc):
+    """The oracle's octave chain (downsample the raw series, re-deredden with W
+    fixed in current samples, re-normalise) against the numpy restatement,
+    over four octaves of a series with a strong trend and red noise; the
+    plausible misreadings (dereddening the previous octave's dereddened, or
+    normalised, series; doubling W in current samples) give visibly
+    different series, so the check separates them."""
+    rng = np.random.default_rng(31)
+    n = 1200
+    t = np.arange(n)
+    x = (rng.standard_normal(n) + 0.02 * t + 3.0 * np.sin(t / 90.0)
+         + np.cumsum(rng.standard_normal(n)) * 0.3).astype(np.float32)
+    cfg = orc.Config(tsamp=1.0, period_min=8.0, period_max=128.0, downsample0=1)
+    _, _, win = orc.plan(cfg, n)
+    assert win == 33  # min(2 * 128, 4 * 8) = 32, made odd
+    got = orc.octave_series(cfg, x)
+    assert len(got) == 4
+    want = _numpy_octaves(x, 1, win, 4)
+    for o in range(4):
+        assert got[o].size == n >> o
+        np.testing.assert_allclose(got[o], want[o], rtol=0, atol=1e-12)
+    # the misreadings differ from it at every later octave
+    raw = x.astype(np.float64)
+    prev = raw - brute_runmed(raw, win)
+    for o in range(1, 4):
+        m = raw.size // 2
+        raw = raw[0:2 * m:2] + raw[1:2 * m:2]
+        resid_of_resid = prev[0:2 * m:2] + prev[1:2 * m:2]
+        resid_of_resid = resid_of_resid - brute_runmed(resid_of_resid, win)
+        prev = raw - brute_runmed(raw, win)
+        doubled = raw - brute_runmed(raw, (win << o) | 1)
+        for alt in (resid_of_resid, doubled):
+            alt = (alt - alt.mean()) / alt.std()
+            assert np.max(np.abs(alt - got[o])) > 1e-3, o
+    # pre-downsampling D0 = 4 feeds the same chain
+    cfg4 = orc.Config(tsamp=0.25, period_min=8.0, period_max=128.0, downsample0=4)
+    got4 = orc.octave_series(cfg4, np.tile(x, 4))
+    want4 = _numpy_octaves(np.tile(x, 4), 4, win, len(got4))
+    for a, b in zip(got4, want4):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
