@@ -1318,11 +1318,14 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
 
 // ---------------------------------------------------------------------------
 // Algorithm 2 (Section 2.2.2, Eq. 5): boxcar first, then for each width the
-// maximum I_max (first position j*), an exclusion window of the 2h+1
-// filtered bins within cyclic distance h of j*, and
-// A_w = (I_max - I_av) / sigma over the other bins; score = max over widths.
-// Sums are taken about w * mean(x) (the mean of every filtered profile) so
-// that the FP32 sums of squares do not cancel; I_av and sigma in FP64.
+// maximum I_max (first position j*), an exclusion window of the 2h+1 profile
+// bins within cyclic distance h of the box's centre (j* + w/2) mod p0, and
+// A_w = (I_max - w I_av) / (sigma sqrt(w)) with I_av and sigma the mean and
+// population standard deviation of the other, unfiltered, profile bins;
+// score = max over widths.  The profile's sum of squares about its mean is
+// taken once; per width only the window's share is summed (its raw bins
+// recovered as differences of the in-block prefix) and subtracted.  FP64
+// per width, by one thread.
 // ---------------------------------------------------------------------------
 template <class T, class C>
 __device__ __forceinline__ T box_at(const T (&c)[C::R], const Sh2<C>& sh, const T* buf, int tid, int w, int r) {
@@ -1387,6 +1390,16 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
         }
         blk_stats(fs, fq, fm, sh);
         const float mean = fs / (float)p0;
+        // the whole profile's sums of (x - mean) and (x - mean)^2
+        float ps = 0.0f, pq = 0.0f, pm = 0.0f;
+#pragma unroll
+        for (int r = 0; r < R2; ++r)
+            if (r < nvalid) {
+                const float d = (float)x[r] - mean;
+                ps += d;
+                pq = fmaf(d, d, pq);
+            }
+        blk_stats(ps, pq, pm, sh);
         // blocked cyclic prefix (as in k_score2)
         const bool one_wrap = nbe * R2 <= 2 * p0;
         const int eb2 = tid + T2;
@@ -1443,14 +1456,12 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
             }
         }
         __syncthreads();
-        double best = -INFINITY, best_av = 0.0;
+        double best = -INFINITY;
         int best_w = 0, best_j = 0;
         for (int wi = 0; wi < wd.n; ++wi) {
             const int w = wd.w[wi];
-            const float ref = (float)w * mean;  // mean of the filtered profile
             T m = B::lowest();
             int mpos = 0x7fffffff;
-            float s1 = 0.0f, s2 = 0.0f;
             if (nvalid > 0) {
 #pragma unroll
                 for (int r = 0; r < R2; ++r) {
@@ -1460,13 +1471,10 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
                             m = bx;
                             mpos = base_pos + r;
                         }
-                        const float d = (float)bx - ref;
-                        s1 += d;
-                        s2 = fmaf(d, d, s2);
                     }
                 }
             }
-            // block: max with first position, and the two sums
+            // block: max with its first position
             float mf = (float)m;
             for (int o = 16; o > 0; o >>= 1) {
                 const float om = __shfl_xor_sync(0xffffffffu, mf, o);
@@ -1475,21 +1483,15 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
                     mf = om;
                     mpos = op;
                 }
-                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             }
             __syncthreads();
             if (lane == 0) {
                 sh.wred[0][warp] = mf;
                 sh.wredi[0][warp] = mpos;
-                sh.wred[1][warp] = s1;
-                sh.wred[2][warp] = s2;
             }
             __syncthreads();
             mf = lane < NW ? sh.wred[0][lane] : -INFINITY;
             mpos = lane < NW ? sh.wredi[0][lane] : 0x7fffffff;
-            s1 = lane < NW ? sh.wred[1][lane] : 0.0f;
-            s2 = lane < NW ? sh.wred[2][lane] : 0.0f;
             for (int o = 16; o > 0; o >>= 1) {
                 const float om = __shfl_xor_sync(0xffffffffu, mf, o);
                 const int op = __shfl_xor_sync(0xffffffffu, mpos, o);
@@ -1497,22 +1499,23 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
                     mf = om;
                     mpos = op;
                 }
-                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             }
             const int jstar = mpos;
-            // sums over the exclusion window around j*
+            const int centre = (int)(((int64_t)jstar + w / 2) % p0);
+            // sums of (x - mean) and its square over the window's profile bins;
+            // bin r's value is the difference of the in-block prefix (the last
+            // bin's: the block total minus the last prefix)
             float w1 = 0.0f, w2 = 0.0f;
             if (nvalid > 0) {
 #pragma unroll
                 for (int r = 0; r < R2; ++r) {
                     const int j = base_pos + r;
-                    int d = j - jstar;
+                    int d = j - centre;
                     if (d < 0) d = -d;
                     d = min(d, p0 - d);
                     if (r < nvalid && d <= h) {
-                        const T bx = box_at(x, sh, buf, tid, w, r);
-                        const float dd = (float)bx - ref;
+                        const T v = B::diff(r + 1 < R2 ? x[r + 1] : tot, x[r]);
+                        const float dd = (float)v - mean;
                         w1 += dd;
                         w2 = fmaf(dd, dd, w2);
                     }
@@ -1535,22 +1538,20 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
                 w2 += __shfl_xor_sync(0xffffffffu, w2, o);
             }
             if (tid == 0 && n_off >= 2) {  // only thread 0 keeps the score: FP64 once per width
-                const double a1 = ((double)s1 - (double)w1) / n_off;        // mean offset from ref
-                const double var = ((double)s2 - (double)w2) / n_off - a1 * a1;
+                const double a1 = ((double)ps - (double)w1) / n_off;  // off-pulse mean - mean
+                const double var = ((double)pq - (double)w2) / n_off - a1 * a1;
                 const double sd = var > 0.0 ? sqrt(var) : 0.0;
-                const double av = (double)ref + a1;
+                const double av = (double)mean + a1;
                 if (sd > 0.0) {
-                    const double a = ((double)mf - av) / sd;
+                    const double a = ((double)mf - (double)w * av) / (sd * sqrt((double)w));
                     if (a > best) {
                         best = a;
                         best_w = wi;
                         best_j = jstar;
-                        best_av = av;
                     }
                 }
             }
         }
-        (void)best_av;
         if (tid == 0) {
             ffa_record out;
             if (best == -INFINITY) {

@@ -7,6 +7,7 @@ import os
 
 import numpy as np
 import pytest
+from parity import check_records, trial_profiles
 
 pytestmark = pytest.mark.gpu
 
@@ -47,12 +48,19 @@ def okw(kw, fold_type):
     return dict(d, fold_type=fold_type)
 
 
-def compare_records(got, ref, tol=SNR_TOL):
-    d = np.abs(got["snr"].astype(np.float64) - ref["snr"])
-    assert d.max() <= tol, (d.max(), int(d.argmax()))
-    assert np.array_equal(got["flags"], ref["flags"])
-    agree = (got["width"] == ref["width"]) & (got["phase"] == ref["phase"])
-    return float(agree.mean())
+def compare_records(orc, ocfg, x, got, ref, tol=SNR_TOL):
+    """S/N within tol, identical flags, width/phase identical except at the
+    oracle's near-ties (top-2 gap < 1e-3); returns the near-tie count."""
+    rows, _, _ = orc.plan(ocfg, x.size)
+    return check_records(got, ref, trial_profiles(orc, ocfg, x, rows), tol=tol)
+
+
+def same_best(got, ref, best, orc):
+    """The identical best (P0, trial, width, phase): the same periodogram index
+    (hence octave, P0 and trial) and the same width and phase there."""
+    assert best == orc.best(ref)
+    assert (int(got["width"][best]), int(got["phase"][best])) == \
+        (int(ref["width"][best]), int(ref["phase"][best]))
 
 
 def plain_kw():
@@ -66,10 +74,10 @@ def test_plain_workload_vs_fp64_oracle(F, orc, dev):
     x = synth.plain_series()
     kw = plain_kw()
     plan, got, cands, best = run(F, dev, kw, x)
-    ref = orc.search(orc.Config(**okw(kw, orc.FOLD_F64)), x, nthreads=os.cpu_count())
-    agree = compare_records(got, ref)
-    assert agree > 0.98
-    assert best == orc.best(ref)
+    ocfg = orc.Config(**okw(kw, orc.FOLD_F64))
+    ref = orc.search(ocfg, x, nthreads=os.cpu_count())
+    compare_records(orc, ocfg, x, got, ref)
+    same_best(got, ref, best, orc)
     e = plan.entries[np.searchsorted(plan.entries["first_trial"], best, side="right") - 1]
     assert e["p0"] == 390
     # the candidate list is the top of the GPU periodogram, best first
@@ -86,24 +94,42 @@ def test_plain_workload_vs_fp32_oracle(F, orc, dev):
     x = synth.plain_series(seed=11)
     kw = plain_kw()
     _, got, _, best = run(F, dev, kw, x)
-    ref = orc.search(orc.Config(**okw(kw, orc.FOLD_F32)), x, nthreads=os.cpu_count())
-    compare_records(got, ref, tol=1e-4)
-    assert best == orc.best(ref)
+    ocfg = orc.Config(**okw(kw, orc.FOLD_F32))
+    ref = orc.search(ocfg, x, nthreads=os.cpu_count())
+    compare_records(orc, ocfg, x, got, ref, tol=1e-4)
+    same_best(got, ref, best, orc)
 
 
 def test_int8_path_matches_int_oracle(F, orc, dev):
+    """The int8 search end to end.  The device's int8 codes equal the oracle's
+    except for 1-LSB flips where 16 z lies on a .5 tie that the two FP64
+    reduction orders round apart (counted); the oracle's exact int fold and
+    scoring of the device's own codes reproduce every GPU record bit for bit;
+    the int8 result's agreement with the FP64 search is stated."""
+    import torch
     from paper_1703_05581_gb300 import synth
     x = synth.plain_series(seed=3)
     kw = dict(plain_kw(), precision=F.FOLD_I8)
     plan, got, _, best = run(F, dev, kw, x)
     ocfg = orc.Config(**okw(kw, orc.FOLD_I8))
-    ref = orc.search(ocfg, x, nthreads=os.cpu_count())
-    # the int8 codes can differ only where FP64 summation order moves 16 z across .5
+    q_orc = orc.octave_series(ocfg, x)[0]
+    resid = F.detrend(F.downsample(torch.from_numpy(x).to(dev), 1), plan.window)
+    q_dev = F.normalise(resid, F.FOLD_I8)[0].cpu().numpy()
+    diff = q_dev.astype(np.int32) - q_orc.astype(np.int32)
+    flips = np.flatnonzero(diff)
+    assert np.all(np.abs(diff) <= 1)
+    z64 = orc.octave_series(orc.Config(**okw(plain_kw(), orc.FOLD_F64)), x)[0]
+    frac = np.abs(16.0 * z64[flips]) % 1.0
+    assert np.all(np.abs(frac - 0.5) < 1e-9), frac
+    print(f"int8 quantiser: {flips.size} 1-LSB flips of {q_dev.size} codes")
+    rows, _, _ = orc.plan(ocfg, x.size)
+    ref = orc.fold_score_rows(orc.FOLD_I8, [q_dev], rows, nthreads=os.cpu_count())
+    assert np.array_equal(got["snr"], ref["snr"].astype(np.float32))
+    assert np.array_equal(got["width"], ref["width"]) and np.array_equal(got["phase"], ref["phase"])
+    assert np.array_equal(got["flags"], ref["flags"])
+    same_best(got, ref, best, orc)
+    # int8 vs FP64: correlation of the periodograms (error stated in the design notes)
     ref_f64 = orc.search(orc.Config(**okw(kw, orc.FOLD_F64)), x, nthreads=os.cpu_count())
-    same = got["snr"] == ref["snr"].astype(np.float32)
-    assert same.mean() > 0.99
-    assert best == orc.best(ref) or abs(best - orc.best(ref)) <= 1
-    # int8 vs FP64 S/N error stated: correlation and best-candidate agreement
     assert np.corrcoef(got["snr"], ref_f64["snr"])[0, 1] > 0.98
 
 
@@ -137,9 +163,10 @@ def test_u8_input_and_predownsampling(F, orc, dev):
     kw = dict(tsamp=1e-3, period_min=0.3, period_max=1.1, duty=0.2, downsample0=4,
               in_type=F.IN_U8)
     _, got, _, best = run(F, dev, kw, x)
-    ref = orc.search(orc.Config(**okw(kw, orc.FOLD_F64)), x, nthreads=os.cpu_count())
-    compare_records(got, ref)
-    assert best == orc.best(ref)
+    ocfg = orc.Config(**okw(kw, orc.FOLD_F64))
+    ref = orc.search(ocfg, x, nthreads=os.cpu_count())
+    compare_records(orc, ocfg, x, got, ref)
+    same_best(got, ref, best, orc)
 
 
 def test_several_octaves_small(F, orc, dev):
@@ -150,9 +177,10 @@ def test_several_octaves_small(F, orc, dev):
     kw = dict(tsamp=512e-6, period_min=0.5, period_max=6.0, duty=0.2)
     plan, got, cands, best = run(F, dev, kw, x)
     assert plan.n_octaves == 4
-    ref = orc.search(orc.Config(**okw(kw, orc.FOLD_F64)), x, nthreads=os.cpu_count())
-    compare_records(got, ref)
-    assert best == orc.best(ref)
+    ocfg = orc.Config(**okw(kw, orc.FOLD_F64))
+    ref = orc.search(ocfg, x, nthreads=os.cpu_count())
+    compare_records(orc, ocfg, x, got, ref)
+    same_best(got, ref, best, orc)
 
 
 def test_edge_cases(F, orc, dev):
@@ -165,9 +193,10 @@ def test_edge_cases(F, orc, dev):
     x = np.random.default_rng(2).standard_normal(41).astype(np.float32)
     kw = dict(tsamp=1.0, period_min=20.0, period_max=21.0, widths=(1, 2))
     plan, got, _, best = run(F, dev, kw, x)
-    ref = orc.search(orc.Config(**okw(kw, orc.FOLD_F64)), x)
+    ocfg = orc.Config(**okw(kw, orc.FOLD_F64))
+    ref = orc.search(ocfg, x)
     assert plan.n_trials == 2
-    compare_records(got, ref)
+    compare_records(orc, ocfg, x, got, ref)
     # workspace too small is rejected on the host
     plan = F.Plan(F.Config(**plain_kw()), 65536)
     xs = torch.zeros(65536, dtype=torch.float32, device=dev)
@@ -245,7 +274,7 @@ def test_survey_workload_sampled(F, orc, dev):
             prof = orc.fold_trial(z[o], p0, md, m, k)
             ref = orc.score_alg1(prof, r["widths"][: r["n_widths"]])
             g = got[int(r["first_trial"]) + k]
-            assert abs(float(g["snr"]) - ref["snr"]) <= SNR_TOL, (o, p0, k)
+            check_records(np.array([g]), np.array([ref]), lambda _: prof)
     # the candidate list starts with the periodogram's best record (with this
     # recipe's red noise Algorithm 1's best is a red-noise detection, not the
     # injected 7.3 s pulsar: the behaviour Section 4.1.2 reports)

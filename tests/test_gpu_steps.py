@@ -5,6 +5,7 @@ import math
 
 import numpy as np
 import pytest
+from parity import check_records
 
 pytestmark = pytest.mark.gpu
 
@@ -170,17 +171,9 @@ def _profiles(rng, count, p0, kind):
 
 
 def _check_records(got, ref, profiles, tol):
-    assert np.all(got["flags"] == ref["flags"])
-    assert np.max(np.abs(got["snr"].astype(np.float64) - ref["snr"])) <= tol
-    mism = (got["width"] != ref["width"]) | (got["phase"] != ref["phase"])
-    # a different (width, phase) is allowed only when it is as good within tolerance
-    for i in np.flatnonzero(mism):
-        x = profiles[i].astype(np.float64)
-        w, j = int(got["width"][i]), int(got["phase"][i])
-        box = x[(j + np.arange(w)) % x.size].sum()
-        snr = (box - w * ref["median"][i]) / (1.4826 * ref["mad"][i] * math.sqrt(w))
-        assert abs(snr - ref["snr"][i]) <= 10 * tol
-    return int(mism.sum())
+    """S/N within tol, identical flags, and width/phase identical except where
+    the oracle's S/N at the GPU's choice is within 1e-3 of its best."""
+    return check_records(got, ref, lambda i: profiles[i].astype(np.float64), tol=tol)
 
 
 @pytest.mark.parametrize("p0,widths", [(1, (1,)), (2, (1, 2)), (9, (1, 2, 4)), (256, (1, 2, 4, 8, 16)),
