@@ -1,24 +1,37 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 FFA period search.
 
-Workload (default ``survey``): one 2^26-sample float32 series at 64 us (white
+Default workload (``survey``): one 2^26-sample float32 series at 64 us (white
 noise + AR(1) red noise + a 7.3 s pulsar), searched over 1-30 s periods with
 per-octave downsampling, the paper's default dereddening window and
 Algorithm 1 widths up to 10 % duty.  One step = the whole search of one
 series (downsampling, dereddening, normalisation, FFA fold and scoring of
-every base period of every octave, candidate extraction).
+every base period of every octave).
 
 Metric: FFA search rate in input samples x trials per second: for every base
 period, (data rows x P0 samples folded) x (M trials produced), summed, per
 second.  ``value`` is timed on the device with CUDA events, inputs already
 resident; ``e2e`` times the same step through the public API from pinned
 host memory (host->device copy of the series and device->host read of the
-candidate list inside the timed region).
+candidate list inside the timed region).  ``roofline`` is the HBM view: the
+algorithmic bytes of a base period (its octave series read once, one 16-byte
+record per trial) over the fold + score time of sampled base periods, and
+the same bytes of the whole search over the step time (``search_frac``).
 
 --impl reference times the CPU oracle (the plain FP64 implementation used
 for parity) on a bounded sample of the same workload on the host cores.
 Multi-GPU (--gpus N under torchrun): every rank searches its own series
 (weak scaling); there is no collective on the data path.
+
+Other measurements (one JSON line each, not the headline):
+  --workload plain              the 65 536-sample parity workload
+  --workload batch [--series S] [--chunk C] [--precision f32|i8]
+                                the DM-trial batch (lengths U[2^22, 2^23] at 512 us)
+  --workload serve [--rate R] [--duration D] [--slots K] [--budget-gb G]
+                                Poisson request stream through the serving loop
+  --kernel fold-score [--p0 P --m-data D --m M --widths W] [--reps R]
+                                one base period's fold and scoring, CUDA events
+  --kernel search               one whole survey search with per-octave phase times
 """
 from __future__ import annotations
 
@@ -29,6 +42,7 @@ import os
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -40,6 +54,8 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "FFA search rate (input samples*trials/s)"
 UNIT = "samples*trials/s"
+# groups of short base periods (fewer rows than this) are folded and scored together
+GROUP_TRIALS = 1024
 
 
 def parse_args():
@@ -48,11 +64,28 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["survey", "plain"], default="survey")
+    ap.add_argument("--workload", choices=["survey", "plain", "batch", "serve"], default="survey")
+    ap.add_argument("--kernel", choices=["fold-score", "search"], default=None)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0,
                     help="target CPU seconds of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # batch
+    ap.add_argument("--series", type=int, default=64)
+    ap.add_argument("--chunk", type=int, default=64)
+    ap.add_argument("--precision", choices=["f32", "i8"], default="f32")
+    # serve
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--duration", type=float, default=60.0)
+    ap.add_argument("--requests", type=int, default=0, help="cap on requests (0: rate x duration)")
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    # kernel
+    ap.add_argument("--p0", type=int)
+    ap.add_argument("--m-data", type=int)
+    ap.add_argument("--m", type=int)
+    ap.add_argument("--widths", type=int, default=12)
+    ap.add_argument("--reps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -75,29 +108,39 @@ def workload(name: str):
     return kw, p["n"], (lambda seed: synth.plain_series(seed=seed)), desc
 
 
+def synth_seed(name: str) -> int:
+    from paper_1703_05581_gb300 import synth
+    return synth.SURVEY["seed"] if name == "survey" else synth.PLAIN["seed"]
+
+
 def plan_units(entries) -> float:
     e = entries
     return float(np.sum(e["m_data"].astype(np.float64) * e["p0"] * e["m_rows"]))
 
 
-def fold_score_bytes(entries, in_bytes: int = 4) -> np.ndarray:
-    """Algorithmic bytes of fold+score per octave: read the octave series once per
-    base period (data rows x P0 samples) and write one 16-byte record per trial."""
-    out = np.zeros(64)
+def entry_bytes(entries, in_bytes: int = 4) -> np.ndarray:
+    """Algorithmic bytes of each base period: its octave series read once (data
+    rows x P0 samples) and one 16-byte record written per trial."""
+    e = entries
+    return in_bytes * e["m_data"].astype(np.float64) * e["p0"] + 16.0 * e["m_rows"]
+
+
+def search_bytes(entries, in_bytes: int = 4) -> float:
+    """Algorithmic bytes of a whole search: every base period's bytes plus the
+    octave downsampling and dereddening (8 bytes in and out per sample of
+    every octave after the first)."""
+    tot = float(entry_bytes(entries, in_bytes).sum())
     for o in np.unique(entries["octave"]):
-        e = entries[entries["octave"] == o]
-        out[o] = float(np.sum(in_bytes * e["m_data"].astype(np.float64) * e["p0"] + 16.0 * e["m_rows"]))
-    return out
+        if o > 0:
+            tot += 16.0 * float(entries["n_octave"][entries["octave"] == o][0])
+    return tot
 
 
-# GB300 FP32/INT32 lane peak for ALU-bound kernels: 152 SMs x 128 lanes x 2070 MHz
-# (the maximum SM clock); one algorithmic operation per lane per clock.
-ALU_LANES = 152 * 128
-ALU_MAX_MHZ = 2070.0
-# DRAM bytes per profile bin of one k_score2 launch (read + write), from the
-# ncu capture summarised in profiles/k_score2_p0_20000_m4096.md:
-# (329.25 MB + 11.89 MB) / (4096 * 20000).  Set to None when the kernel changes.
-SCORE_DRAM_BYTES_PER_ELEM = (329247232 + 11889920) / (4096 * 20000)
+def fold_adds(entries) -> np.ndarray:
+    """The FFA's additions per base period, M * P0 * log2(M): the measure the
+    CPU sample is scaled by."""
+    m = entries["m_rows"].astype(np.float64)
+    return m * entries["p0"] * np.log2(np.maximum(m, 2.0))
 
 
 def score_ops(entries) -> np.ndarray:
@@ -109,10 +152,12 @@ def score_ops(entries) -> np.ndarray:
     return e["m_rows"].astype(np.float64) * e["p0"] * (1.0 + 2.0 * e["n_widths"] + 3.0)
 
 
-def sampled(entries, octave, sample):
-    """Entries whose launches the library times: every sample-th of the octave."""
-    idx = np.flatnonzero(entries["octave"] == octave)
-    return entries[idx[::sample]]
+def sampled_singles(entries, octave, sample):
+    """Base periods whose launches the library times one by one: every
+    sample-th of the octave, when it is not folded in a group."""
+    idx = np.flatnonzero(entries["octave"] == octave)[::sample]
+    sub = entries[idx]
+    return sub[sub["m_rows"] >= GROUP_TRIALS]
 
 
 def measured_peaks():
@@ -121,6 +166,13 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def alu_peak_tops() -> float:
+    """FP32/INT32 lane peak: SMs x 128 lanes x the maximum SM clock (2070 MHz)."""
+    import torch
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return nsm * 128 * 2070e6 / 1e12
 
 
 class ClockSampler:
@@ -184,27 +236,65 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample)
 # ---------------------------------------------------------------------------
-def cpu_oracle_sample(kw, n, make, budget_s: float):
-    """Time the oracle on a bounded sample of the workload and scale it to the
-    metric.  Sample: the running-median dereddening of a 2^20-sample slice
-    (scaled by the samples of every octave) plus the fold + scoring of a few
-    base periods spread over the octaves (scaled by their share of the
-    workload's samples x trials)."""
-    import oracle
-    oracle.build()
+def cpu_info() -> dict:
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"cpu_model": model or "unknown", "nproc": os.cpu_count(), "machine": platform.machine()}
+
+
+def _host_threads() -> int:
     threads = os.cpu_count() or 1
-    try:  # each base period folds in up to ~3 GB of host memory: bound the threads by it
+    try:  # a base period folds in up to ~3 GB of host memory: bound the threads by it
         with open("/proc/meminfo") as f:
-            avail_kb = next(int(l.split()[1]) for l in f if l.startswith("MemAvailable"))
+            avail_kb = next(int(line.split()[1]) for line in f if line.startswith("MemAvailable"))
         threads = max(1, min(threads, int(avail_kb / (4 << 20))))
     except (OSError, StopIteration, ValueError):
         pass
+    return threads
+
+
+def _stride_sample(rows, n_pick: int):
+    """Every k-th base period of the plan (systematic, all octaves in proportion)."""
+    n_pick = max(1, min(n_pick, rows.size))
+    k = rows.size / n_pick
+    idx = np.unique((k * (np.arange(n_pick) + 0.5)).astype(int))
+    return rows[idx], int(round(k))
+
+
+def cpu_oracle_sample(kw, n, make, budget_s: float):
+    """Time the oracle on a bounded sample of the workload, on one thread and
+    on every usable host core, and scale each to the whole plan by the FFA's
+    addition count (sum of M * P0 * log2 M).  The sample is every k-th base
+    period of the plan, k chosen so that each run takes about half the
+    budget; the dereddening of a 2^20-sample slice is timed on one thread (the
+    oracle's dereddening is sequential) and scaled by every octave's samples."""
+    import oracle
+    oracle.build()
+    threads = _host_threads()
     ocfg = oracle.Config(**{k: v for k, v in kw.items() if k != "widths"},
                          widths=kw.get("widths", ()), fold_type=oracle.FOLD_F64)
-    rows, nt, win = oracle.plan(ocfg, n)
+    rows, _, win = oracle.plan(ocfg, n)
     total_units = plan_units(rows)
+    w_all = fold_adds(rows)
+    w_total = float(w_all.sum())
     x = make(7)
-    # dereddening of a slice, single thread, scaled to every octave's samples
     sl = min(n, 1 << 20)
     raw = oracle.downsample(x[:sl], 1)
     t0 = time.perf_counter()
@@ -214,28 +304,39 @@ def cpu_oracle_sample(kw, n, make, budget_s: float):
     n_oct = int(rows["octave"].max()) + 1
     all_samples = sum(n >> o for o in range(n_oct))
     t_detrend = t_med * all_samples / sl
-    # fold + score: one base period per host thread, evenly spaced over the plan (so the
-    # octaves are represented in proportion to their base periods), run in parallel
-    idx = np.unique(np.linspace(0, rows.size - 1, min(threads, rows.size)).astype(int))
-    sub = rows[idx]
-    n_oct = int(rows["octave"].max()) + 1
-    z = oracle.octave_series(ocfg, x[: n]) if n <= (1 << 22) else None
-    if z is None:
-        # the dereddened series themselves are not needed for timing: fold white noise
-        z = [np.random.default_rng(o).standard_normal(n >> o) for o in range(n_oct)]
+    # the octave series only feed the timing: white noise of each octave's length
+    z = [np.random.default_rng(o).standard_normal(n >> o) for o in range(n_oct)]
+    # calibrate on the cheapest base period: additions per second on one thread
+    i0 = int(np.argmin(w_all))
     t0 = time.perf_counter()
-    oracle.fold_score_rows(oracle.FOLD_F64, z, sub, nthreads=threads)
-    t_fs = time.perf_counter() - t0
-    sample_units = plan_units(sub)
-    t_total = t_fs * total_units / sample_units + t_detrend
-    rate = total_units / t_total
+    oracle.fold_score_rows(oracle.FOLD_F64, z, rows[i0:i0 + 1], nthreads=1)
+    rate1 = float(w_all[i0]) / max(time.perf_counter() - t0, 1e-6)
+    res = {}
+    for label, nt, share in (("single", 1, 0.35), ("all", threads, 0.55)):
+        want = budget_s * share * rate1 * nt  # additions that fit the time
+        n_pick = int(max(nt, min(rows.size, want / (w_total / rows.size))))
+        sub, k = _stride_sample(rows, n_pick)
+        t0 = time.perf_counter()
+        oracle.fold_score_rows(oracle.FOLD_F64, z, sub, nthreads=nt)
+        t_fs = time.perf_counter() - t0
+        w_sub = float(fold_adds(sub).sum())
+        t_full = t_fs * w_total / w_sub + t_detrend
+        res[label] = {"value": total_units / t_full, "threads": nt, "base_periods": int(sub.size),
+                      "stride": k, "sample_s": t_fs, "full_step_s": t_full}
+    a, s1 = res["all"], res["single"]
+    info = cpu_info()
     return {
-        "value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-        "sample": (f"oracle (FP64) fold+Algorithm 1 of {sub.size} base periods spread over "
-                   f"{n_oct} octaves ({sample_units:.3g} of {total_units:.3g} samples*trials, "
-                   f"{t_fs:.1f} s on {threads} threads) plus the running median of a {sl}-sample "
-                   f"slice ({t_med:.1f} s, 1 thread), both scaled to the whole workload"),
-        "est_step_s": t_total,
+        "value": a["value"], "unit": UNIT, "cores": a["threads"], "kind": "oracle",
+        "sample": (f"oracle (FP64) fold + Algorithm 1 of every {a['stride']}th base period "
+                   f"({a['base_periods']} of {rows.size}, {a['sample_s']:.1f} s on {a['threads']} threads) and "
+                   f"of every {s1['stride']}th ({s1['base_periods']}, {s1['sample_s']:.1f} s on 1 thread), "
+                   f"each scaled by the plan's sum of M*P0*log2(M); plus the running median of a "
+                   f"{sl}-sample slice ({t_med:.2f} s, 1 thread) scaled by every octave's samples"),
+        "single_thread": {"value": s1["value"], "unit": UNIT, "cores": 1,
+                          "extrapolated_step_s": s1["full_step_s"]},
+        "extrapolated_step_s": a["full_step_s"],
+        "sample_wall_s": a["sample_s"] + s1["sample_s"] + t_med,
+        **info,
     }
 
 
@@ -243,27 +344,51 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    kw, n, make, desc = workload(args.workload)
-    per_step = max(5.0, 60.0 / max(1, args.steps + args.warmup))
-    vals = []
+    kw, n, make, desc = workload(args.workload if args.workload in ("survey", "plain") else "survey")
+    per_step = max(4.0, 150.0 / max(1, args.steps + args.warmup))
+    vals, walls = [], []
+    r = None
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         r = cpu_oracle_sample(kw, n, make, per_step)
         if i >= args.warmup:
             vals.append(r["value"])
+            walls.append(time.perf_counter() - t0)
     v = float(np.median(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["est_step_s"] * 1e3,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(walls)) * 1e3,
+            "extrapolated_full_step_ms": r["extrapolated_step_s"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": desc,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
+                             "sample": r["sample"], "cpu_model": r["cpu_model"], "nproc": r["nproc"],
+                             "single_thread": r["single_thread"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------
-# GPU arm
+# GPU arm: the survey (or plain) search
 # ---------------------------------------------------------------------------
+def kernel_shares(plan, phase_ms, phase_cnt, steps, step_ms):
+    """Share of the step's device time of the preparation, the fold passes and
+    the scorer over the whole search: each octave's fold + score time split
+    by the fold/score ratio of its sampled base periods (or groups)."""
+    prep = float(phase_ms[0].sum()) / steps
+    fold = score = 0.0
+    for o in range(plan.n_octaves):
+        tot = float(phase_ms[1][o]) / steps
+        f = float(phase_ms[2][o] + phase_ms[4][o])
+        s = float(phase_ms[3][o] + phase_ms[5][o])
+        r = f / (f + s) if f + s > 0 else 0.5
+        fold += tot * r
+        score += tot * (1.0 - r)
+    other = max(step_ms - prep - fold - score, 0.0)
+    return {"prep": prep / step_ms, "fold": fold / step_ms, "score": score / step_ms, "other": other / step_ms,
+            "ms_per_step": {"prep": prep, "fold": fold, "score": score, "other": other}}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -293,7 +418,6 @@ def run_gpu(args):
     status = ffa.status_word(dev)
     stream = torch.cuda.Stream(dev)
     units = plan_units(plan.entries)
-    fs_bytes = fold_score_bytes(plan.entries)
 
     def step():
         ffa.search(plan, xs, workspace=ws, records=rec, status=status, stream=stream)
@@ -356,51 +480,50 @@ def run_gpu(args):
     if rank == 0:
         value = units * world * args.steps / (ms_max / 1e3)
         e2e_value = units * world * args.e2e_steps / e2e_s
+        step_ms = ms_max / args.steps
         peak, peak_kind = measured_peaks()
-        # fold + score phase: HBM view (algorithmic bytes of the search's fold+score)
-        fs_ms = phase_ms[1]
-        fs_cnt = np.maximum(phase_cnt[1], 1)
-        oct_ms = fs_ms / fs_cnt
-        tot_bytes = float(np.sum(fs_bytes[: len(oct_ms)] * (phase_cnt[1] > 0)))
-        tot_ms = float(np.sum(oct_ms * (phase_cnt[1] > 0)))
-        hbm_achieved = tot_bytes / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else 0.0
-        prep_ms = float(np.sum(phase_ms[0] / np.maximum(phase_cnt[0], 1)))
-        # dominant kernel: k_score2, timed per launch on sampled base periods
-        sc_ops = sc_ms = sc_elems = sc_n = fo_ms = 0.0
+        # the hot path's unit: fold + score of a base period, sampled every 64th per octave
+        b_s = t_s = ops = sc_ms = bins = 0.0
+        n_s = 0
         for o in range(plan.n_octaves):
             if phase_cnt[3][o] == 0:
                 continue
-            sub = sampled(plan.entries, o, ffa.TIMING_SAMPLE)
+            sub = sampled_singles(plan.entries, o, ffa.TIMING_SAMPLE)
             reps = phase_cnt[3][o] / max(len(sub), 1)  # timed steps
-            sc_ops += float(score_ops(sub).sum()) * reps
-            sc_elems += float((sub["m_rows"].astype(np.float64) * sub["p0"]).sum()) * reps
+            b_s += float(entry_bytes(sub).sum()) * reps
+            ops += float(score_ops(sub).sum()) * reps
+            bins += float((sub["m_rows"].astype(np.float64) * sub["p0"]).sum()) * reps
+            t_s += float(phase_ms[2][o] + phase_ms[3][o])
             sc_ms += float(phase_ms[3][o])
-            fo_ms += float(phase_ms[2][o])
-            sc_n += float(phase_cnt[3][o])
-        alu_peak = ALU_LANES * ALU_MAX_MHZ * 1e6 / 1e12
-        alu_achieved = sc_ops / (sc_ms / 1e3) / 1e12 if sc_ms > 0 else 0.0
-        traffic = (SCORE_DRAM_BYTES_PER_ELEM * sc_elems / sc_n
-                   if SCORE_DRAM_BYTES_PER_ELEM and sc_n else None)
+            n_s += int(phase_cnt[3][o])
+        achieved = b_s / (t_s / 1e3) / 1e9 if t_s > 0 else 0.0
+        s_bytes = search_bytes(plan.entries)
+        search_gbs = s_bytes / (step_ms / 1e3) / 1e9
+        alu_pk = alu_peak_tops()
+        alu_achieved = ops / (sc_ms / 1e3) / 1e12 if sc_ms > 0 else 0.0
+        traffic = (DRAM_BYTES_PER_BIN * bins / n_s) if (DRAM_BYTES_PER_BIN and n_s) else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(desc, l2="inputs and fold planes larger than L2 (no flush needed)",
                            trials=int(plan.n_trials), base_periods=int(plan.n_periods),
                            autotuned_fold_shapes=int(n_tuned),
                            samples_x_trials=units),
-            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak,
-                         "unit": "TFLOP/s", "frac": alu_achieved / alu_peak, "traffic": traffic,
-                         "kernel": "k_score2 (Algorithm 1 + fused last FFA stage), mean over "
-                                   f"{int(sc_n)} sampled launches",
-                         "ops": "per bin: last-stage add + 2 per width + 3 (selections, deviation)",
-                         "peak_from": "152 SMs x 128 FP32/INT32 lanes x 2070 MHz",
-                         "score_ms_per_launch": sc_ms / max(sc_n, 1),
-                         "fold_ms_per_launch": fo_ms / max(sc_n, 1),
-                         "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": peak, "peak_kind": peak_kind,
-                                 "frac": hbm_achieved / peak,
-                                 "bytes": "algorithmic: 4*M_data*P0 + 16*M per base period"},
-                         "phase_ms_per_step": {"prep": prep_ms, "fold_score": tot_ms}},
+            "roofline": {
+                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": ("fold passes (k_fold) + Algorithm 1 scorer with the last FFA stage fused "
+                           f"(k_score2) of one base period; {n_s} sampled base periods"),
+                "bytes": "algorithmic per base period: 4*M_data*P0 (series read once) + 16*M (records)",
+                "search_frac": search_gbs / peak, "search_gbs": search_gbs, "search_bytes": s_bytes,
+                "alu": {"kernel": "k_score2", "achieved_tops": alu_achieved, "peak_tops": alu_pk,
+                        "frac": alu_achieved / alu_pk, "unit": "T int/FP32 ops/s",
+                        "ops": "per bin: last-stage add + 2 per width + 3 (selections, deviation)",
+                        "peak_from": "SMs x 128 FP32/INT32 lanes x 2070 MHz",
+                        "ms_per_launch": sc_ms / max(n_s, 1)},
+            },
+            "kernel_shares": kernel_shares(plan, phase_ms, phase_cnt, args.steps, step_ms),
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
                     "d2h_bytes_per_step": d2h // max(1, args.e2e_steps)},
@@ -410,22 +533,280 @@ def run_gpu(args):
         }
         if not args.no_cpu_baseline:
             cb = cpu_oracle_sample(kw, n, make, args.cpu_budget_s)
-            cb.pop("est_step_s", None)
+            for k in ("extrapolated_step_s", "sample_wall_s"):
+                cb.pop(k, None)
             line["cpu_baseline"] = cb
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def synth_seed(name: str) -> int:
+# DRAM bytes (read + write) per folded-profile bin of one base period's fold
+# and scoring launches, from an ncu capture of P0 = 20 000, M = 4096 (None
+# until the current kernels are captured).
+DRAM_BYTES_PER_BIN = None
+
+
+# ---------------------------------------------------------------------------
+# Batched searches (DM trials) and serving
+# ---------------------------------------------------------------------------
+BATCH_KW = dict(tsamp=512e-6, period_min=0.5, period_max=20.0, duty=0.2)
+
+
+def batch_series(count: int, seed: int = 3, pool_size: int = 16):
+    """The DM-trial batch recipe (lengths uniform in [2^22, 2^23] at 512 us,
+    white + AR(1) red noise, 5 % with pulsars of 0.5-20 s, FWHM 1-5 %, S/N
+    8-20), yielded one series at a time.  Series are built from `pool_size`
+    generated noise realisations, each series a cyclic shift of one of them
+    cut to its own length, plus its own pulsar: generating 1024 independent
+    series on the host would pace the measurement, and the search's cost does
+    not depend on which noise it sees."""
     from paper_1703_05581_gb300 import synth
-    return synth.SURVEY["seed"] if name == "survey" else synth.PLAIN["seed"]
+    specs = synth.batch_specs(count, 1 << 22, 1 << 23, seed)
+    pool = [synth.make_series(synth.SeriesSpec(n=1 << 23, seed=seed * 7919 + i, red_coef=0.999, red_std=0.3))
+            for i in range(min(pool_size, count))]
+    rng = np.random.default_rng(seed + 17)
+    for i, sp in enumerate(specs):
+        base = np.roll(pool[i % len(pool)], int(rng.integers(0, 1 << 23)))[: sp.n].copy()
+        if sp.pulsar_period is not None:
+            base += synth.gaussian_pulse_train(sp.n, sp.pulsar_period, sp.pulsar_fwhm_frac, float(rng.random()),
+                                               sp.pulsar_snr).astype(np.float32)
+        yield base
+
+
+def run_batch(args):
+    import torch
+
+    from paper_1703_05581_gb300 import ffa
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    prec = ffa.FOLD_F32 if args.precision == "f32" else ffa.FOLD_I8
+    xs = [torch.from_numpy(x).to(dev) for x in batch_series(args.series)]
+    plans = [ffa.Plan(ffa.Config(**BATCH_KW, precision=prec), int(x.numel())) for x in xs]
+    chunk = max(1, min(args.chunk, len(xs)))
+    units = sum(plan_units(p.entries) for p in plans)
+    in_b = 4 if prec == ffa.FOLD_F32 else 1
+    bytes_alg = sum(search_bytes(p.entries, in_b) for p in plans)
+    ws = torch.empty(max(ffa.batch_workspace_bytes(plans[i:i + chunk]) for i in range(0, len(plans), chunk)),
+                     dtype=torch.uint8, device=dev)
+    n_rec = max(p.n_trials for p in plans)
+    rec_pool = torch.empty((chunk, max(n_rec, 1), 4), dtype=torch.int32, device=dev)
+    recs = [rec_pool[i] for i in range(chunk)]
+    st = ffa.status_word(dev)
+    stream = torch.cuda.Stream(dev)
+
+    def one_pass():
+        for i in range(0, len(plans), chunk):
+            pp = plans[i:i + chunk]
+            ffa.search_batch(pp, xs[i:i + chunk], workspace=ws, records=recs[:len(pp)], status=st, stream=stream)
+
+    ffa.autotune(plans[0], torch.empty(plans[0].workspace_bytes, dtype=torch.uint8, device=dev), stream=stream)
+    ffa.search_batch(plans[:chunk], xs[:chunk], workspace=ws, records=recs[:min(chunk, len(plans))], status=st,
+                     stream=stream)  # warm-up
+    ffa.wait(st, stream=stream)
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ffa.launch_count()
+    e0.record(stream)
+    one_pass()
+    e1.record(stream)
+    e1.synchronize()
+    launches = ffa.launch_count() - l0
+    clocks = sampler.stop()
+    ffa.wait(st, stream=stream)
+    ms = e0.elapsed_time(e1)
+    peak, peak_kind = measured_peaks()
+    gbs = bytes_alg / (ms / 1e3) / 1e9
+    print(json.dumps({
+        "metric": METRIC + ", batch", "value": units / (ms / 1e3), "unit": UNIT, "ms": ms,
+        "series": len(xs), "chunk": chunk, "precision": args.precision,
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                     "peak_kind": peak_kind, "bytes": bytes_alg,
+                     "bytes_def": f"per base period {in_b}*M_data*P0 + 16*M, plus 16 B per octave sample"},
+        "gpu_launches": int(launches), "clocks": clocks,
+        "config": {"workload": "batch: lengths U[2^22, 2^23] at 512 us, white + AR(1) red noise, 5 % pulsars; "
+                               "0.5-20 s, duty 0.2", "input": "series resident on the device",
+                   "records": f"{chunk} record buffers reused chunk after chunk"},
+    }), flush=True)
+
+
+def serve_requests(rate: float, count: int, seed: int, pool: np.ndarray):
+    """Poisson stream: lengths log-uniform in [2^20, 2^25] at 64 us; minimum
+    period log-uniform in [0.5 s, min(30 s, T_obs / 16)], maximum
+    min(60 s, P_min * 2^U{1..3}, T_obs / 8); half FP32, half int8; 5 % carry a
+    pulsar; D0 the smallest power of two keeping P_min within 16384 bins.
+    Series are slices of one pre-generated pinned noise buffer."""
+    from paper_1703_05581_gb300 import ffa, synth
+    tsamp = 64e-6
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(count):
+        if rate > 0:
+            t += float(rng.exponential(1.0 / rate))
+        n = int(2 ** rng.uniform(20, 25))
+        t_obs = n * tsamp
+        pmin = float(np.exp(rng.uniform(np.log(0.5), np.log(min(30.0, t_obs / 16)))))
+        pmax = min(60.0, pmin * 2 ** int(rng.integers(1, 4)), t_obs / 8)
+        off = int(rng.integers(0, pool.size - n))
+        x = pool[off:off + n]
+        if rng.random() < 0.05:
+            x = x.copy()
+            p = float(rng.uniform(pmin, pmax)) / tsamp
+            x += synth.gaussian_pulse_train(n, p, float(rng.uniform(0.01, 0.05)), float(rng.random()),
+                                            float(rng.uniform(8.0, 20.0))).astype(np.float32)
+        prec = ffa.FOLD_I8 if rng.random() < 0.5 else ffa.FOLD_F32
+        d0 = 1
+        while pmin / (tsamp * d0) > 16384:
+            d0 *= 2
+        out.append((t, ffa.Config(tsamp=tsamp, period_min=pmin, period_max=pmax, precision=prec, downsample0=d0),
+                    x))
+    return out
+
+
+def run_serve(args):
+    import torch
+
+    from paper_1703_05581_gb300 import ffa
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    count = args.requests if args.requests > 0 else max(1, int(round(args.rate * args.duration)))
+    pool = torch.empty(1 << 26, dtype=torch.float32).pin_memory().numpy()
+    pool[:] = np.random.default_rng(5).standard_normal(pool.size, dtype=np.float32)
+    reqs = serve_requests(args.rate, count, 6, pool)
+    srv = ffa.Server(int(args.budget_gb * (1 << 30)), n_slots=args.slots)
+    tickets = [None] * len(reqs)
+    trace = []  # (time, in flight, queued)
+    done = threading.Event()
+
+    def watch(t0):
+        while not done.is_set():
+            q, f, used = srv.stats()
+            trace.append((time.perf_counter() - t0, f, q, used))
+            time.sleep(0.02)
+
+    def feed(t0):
+        for i, (ta, c, x) in enumerate(reqs):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = srv.submit(c, x, snr_min=8.0, top_k=16)
+
+    t0 = time.perf_counter()
+    wt = threading.Thread(target=watch, args=(t0,), daemon=True)
+    wt.start()
+    ft = threading.Thread(target=feed, args=(t0,))
+    ft.start()
+    lat, qd, runs = [], [], []
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(0.001)
+        _, _, _, tm = srv.wait(tickets[i])
+        qd.append(tm[0])
+        runs.append(tm[1])
+        lat.append(tm[2])
+    wall = time.perf_counter() - t0
+    ft.join()
+    done.set()
+    srv.close()
+    tot_units = sum(plan_units(ffa.Plan(c, x.size).entries) for _, c, x in reqs)
+    lat = np.array(lat)
+    tr = np.array(trace) if trace else np.zeros((1, 4))
+    busy = tr[:, 1] > 0
+    print(json.dumps({
+        "metric": "FFA serving latency", "offered_rate_req_s": args.rate, "requests": len(reqs),
+        "arrival_span_s": reqs[-1][0] if reqs else 0.0, "slots": args.slots,
+        "budget_bytes": int(args.budget_gb * (1 << 30)), "peak_arena_bytes": int(tr[:, 3].max()),
+        "wall_s": wall, "throughput_req_s": len(reqs) / wall, "throughput_samples_trials_s": tot_units / wall,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(lat.mean())},
+        "queued_ms": {"p50": float(np.percentile(qd, 50)), "p99": float(np.percentile(qd, 99))},
+        "service_ms": {"p50": float(np.percentile(runs, 50)), "p99": float(np.percentile(runs, 99))},
+        "in_flight": {"mean_while_busy": float(tr[busy, 1].mean()) if busy.any() else 0.0,
+                      "max": int(tr[:, 1].max()), "fraction_ge2": float(np.mean(tr[busy, 1] >= 2)) if busy.any() else 0.0},
+        "workload": "lengths 2^20-2^25 at 64 us, periods 0.5-60 s, half FP32 / half int8, 5 % pulsars",
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Kernel-level timings (the commands of the ncu summaries)
+# ---------------------------------------------------------------------------
+SURVEY_SHAPES = [(15625, 4294, 8192, 12), (20000, 3355, 4096, 12), (31249, 2147, 4096, 13),
+                 (15625, 268, 512, 12)]
+
+
+def run_kernel(args):
+    import ctypes as C
+
+    import torch
+
+    from paper_1703_05581_gb300 import ffa
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if args.kernel == "search":
+        kw, n, make, _ = workload("survey")
+        plan = ffa.Plan(ffa.Config(**kw), n)
+        x = torch.from_numpy(make(2)).to(dev)
+        ws, rec, st = plan.workspace(dev), plan.records(dev), ffa.status_word(dev)
+        ffa.autotune(plan, ws)
+        ffa.timing_read()
+        ffa.timing_enable(True)
+        t0 = time.time()
+        ffa.search(plan, x, workspace=ws, records=rec, status=st)
+        ffa.wait(st)
+        t1 = time.time()
+        ffa.timing_enable(False)
+        ms, cnt = ffa.timing_read()
+        print(json.dumps({"search_wall_s": t1 - t0, "trials": plan.n_trials, "base_periods": plan.n_periods,
+                          "prep_ms_per_octave": np.round(ms[0][:plan.n_octaves], 3).tolist(),
+                          "fold_score_ms_per_octave": np.round(ms[1][:plan.n_octaves], 3).tolist(),
+                          "shares": kernel_shares(plan, ms, cnt, 1, (t1 - t0) * 1e3)}), flush=True)
+        return
+    shapes = SURVEY_SHAPES if args.p0 is None else [(args.p0, args.m_data, args.m, args.widths)]
+    for p0, md, m, nw in shapes:
+        z = torch.randn(md * p0 + 1, device=dev, dtype=torch.float32)
+        plane = torch.empty((m, p0), device=dev)
+        tmp = torch.empty_like(plane)
+        widths = np.array([2 ** i for i in range(nw)], np.int32)
+        rec = torch.empty((m, 4), dtype=torch.int32, device=dev)
+        st = ffa.status_word(dev)
+        s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+        def fold():
+            ffa._check(ffa._lib.ffa_fold(ffa._ptr(z), ffa.FOLD_F32, p0, md, m, ffa._ptr(plane),
+                                         ffa._ptr(tmp), s))
+
+        def score():
+            ffa._check(ffa._lib.ffa_score(ffa._ptr(plane), ffa.FOLD_F32, m, p0,
+                                          widths.ctypes.data_as(C.c_void_p), nw, ffa._ptr(rec),
+                                          ffa._ptr(st), s))
+
+        for f, name in ((fold, "fold"), (score, "score")):
+            f()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.reps):
+                f()
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / args.reps
+            print(json.dumps({"p0": p0, "m_data": md, "m": m, "kernel": name, "ms": round(t, 4),
+                              "gelem_s": round(m * p0 / t / 1e6, 2)}), flush=True)
 
 
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.kernel is not None:
+        run_kernel(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

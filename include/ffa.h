@@ -141,6 +141,13 @@ ffa_status ffa_plan_info(const ffa_plan* plan, int64_t* n_periods, int64_t* n_tr
 /* Copy the first `cap` plan entries (periodogram order) to host memory. */
 ffa_status ffa_plan_entries(const ffa_plan* plan, ffa_plan_entry* out, int64_t cap);
 
+/* Trial periods in seconds of periodogram records [trial_begin,
+ * trial_begin + count), written to host memory `out`: Eq. 2 with the padded
+ * N = M * P0 (Section 2.1), i.e. trial k of a base period of P0 bins and M
+ * rows at octave o has period (P0 + k / (M - 1)) * tsamp * D0 * 2^o (P0 for
+ * M = 1).  Host only.  FFA_ERR_ARG for a range outside the periodogram. */
+ffa_status ffa_plan_periods(const ffa_plan* plan, int64_t trial_begin, int64_t count, double* out);
+
 /* ---- the search ------------------------------------------------------------ */
 
 /* Run the whole search (Section 2.3 pipeline) on the n-sample device series
@@ -160,6 +167,30 @@ ffa_status ffa_search(const ffa_plan* plan, const void* d_series, void* d_worksp
 ffa_status ffa_search_entries(const ffa_plan* plan, const void* d_series, int64_t entry_begin,
                               int64_t entry_end, void* d_workspace, size_t workspace_bytes,
                               ffa_record* d_records, int32_t* d_status, void* stream);
+
+/* Debug outputs of the search, the extra output streams ffancy offers beside
+ * the periodogram (Section 2.3: the dereddened copy of the input series and
+ * the full suite of folded profiles of an FFA execution).  Both run the
+ * search's own preparation of the octave (D0 sums, downsampling chain,
+ * dereddening, normalisation) on d_series in the workspace.
+ *
+ * ffa_search_series: octave `octave`'s series, n_octave samples of it, copied
+ * to d_out: what = FFA_DUMP_RESID gives the dereddened series (double,
+ * x - running median, before normalisation); FFA_DUMP_Z gives the fold input
+ * (float z, or the int8 code for precision FFA_FOLD_I8).
+ * ffa_search_plane: every folded profile of plan entry `entry`: all M trials,
+ * all FFA stages applied (on the search's own padded-pitch planes), row k =
+ * trial k, packed densely as M * P0 elements (float, or int32 for precision
+ * FFA_FOLD_I8) into d_plane.
+ * Asynchronous on `stream`; FFA_ERR_ARG for an octave or entry outside the
+ * plan, FFA_ERR_OOM for a short workspace. */
+#define FFA_DUMP_RESID 0
+#define FFA_DUMP_Z 1
+ffa_status ffa_search_series(const ffa_plan* plan, const void* d_series, int32_t octave, int32_t what,
+                             void* d_workspace, size_t workspace_bytes, void* d_out, int32_t* d_status,
+                             void* stream);
+ffa_status ffa_search_plane(const ffa_plan* plan, const void* d_series, int64_t entry, void* d_workspace,
+                            size_t workspace_bytes, void* d_plane, int32_t* d_status, void* stream);
 
 /* ffa_search plus the persistence score of Section 5 for every trial:
  * d_persist[t] (uint32, n_trials of them) = the number of above-cutoff
@@ -182,10 +213,23 @@ ffa_status ffa_search_persistence(const ffa_plan* plan, const void* d_series, vo
 ffa_status ffa_autotune(const ffa_plan* plan, void* d_workspace, size_t workspace_bytes, void* stream,
                         int32_t* n_tuned);
 
-/* A batch of series (e.g. dedispersion trials of uneven length), each with
- * its own plan: series i is searched with plans[i] into d_records[i] (host
- * arrays of `count` pointers).  One workspace, at least the largest plan's
- * workspace_bytes, serves every series in turn on `stream`. */
+/* A batch of series (e.g. dedispersion trials of uneven length) with one
+ * configuration: plans[i] (all made from the same ffa_search_config, for
+ * each series' own length; FFA_ERR_ARG otherwise) searches the device series
+ * d_series[i] into d_records[i] (host arrays of `count` pointers).  The
+ * batch runs octave by octave: every series' octave is prepared into its own
+ * slice of the workspace, then base periods of all series are folded and
+ * scored together -- those with the same rows, widths and scorer shape share
+ * one set of fold launches and one persistent scorer launch, each reading its
+ * own series and writing its own records -- so a batch of short series fills
+ * the GPU and takes a fraction of the launches of one search per series.
+ * Each record equals the one ffa_search gives for that series alone (same
+ * kernels, add tree and scorer shape).  d_workspace: at least
+ * ffa_batch_workspace_bytes of device memory, 256-byte aligned (it holds
+ * every series' raw and normalised octave series: about 9 bytes per FP32
+ * input sample, plus two plane buffers).  Plans with persistence are
+ * FFA_ERR_UNSUPPORTED (search them one by one).  Asynchronous on `stream`. */
+ffa_status ffa_batch_workspace_bytes(const ffa_plan* const* plans, int32_t count, size_t* bytes);
 ffa_status ffa_search_batch(const ffa_plan* const* plans, const void* const* d_series, int32_t count,
                             void* d_workspace, size_t workspace_bytes, ffa_record* const* d_records,
                             int32_t* d_status, void* stream);
@@ -362,12 +406,16 @@ ffa_status ffa_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_da
  * FFA_NOALLOC_FOLD_MAX_ELEMS, else FFA_ERR_UNSUPPORTED with a message.
  * The first call on a device looks up the array's device address (a
  * cudaGetSymbolAddress, once per device, with that device current); make that
- * first call before any stream capture.  No cudaMalloc, cudaFree or other
- * allocating routine is called.  All calls share the array and it keeps the
- * last call's contents; nothing in it needs to start at zero because every
- * element read has first been written by the same call.  Calls that overlap
- * on the GPU (different streams, threads or processes sharing the context)
- * race on the array: serialise them.  Results equal ffa_fold's bit for bit. */
+ * first call before any stream capture.  A cudaDeviceReset or any other
+ * re-creation of the device's context reloads the array: the next call sees
+ * the new context's id and looks the address up again (that call is again a
+ * first call).  No cudaMalloc, cudaFree or other allocating routine is
+ * called.  All calls share the array and it keeps the last call's contents;
+ * nothing in it needs to start at zero because every element read has first
+ * been written by the same call.  Calls from streams or host threads of one
+ * process that overlap on the GPU race on the array: serialise them.  (Each
+ * process has its own copy.)  Results equal ffa_fold's bit for bit.
+ * m_rows * p0 is checked without overflow. */
 #define FFA_NOALLOC_FOLD_MAX_ELEMS (8 * 1024 * 1024)
 ffa_status ffa_fold_noalloc(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
                             int64_t m_rows, void* d_plane, void* stream);
@@ -384,10 +432,14 @@ ffa_status ffa_score(const void* d_profiles, int32_t precision, int64_t count, i
  * around phases of every octave: 0 = series preparation (downsampling,
  * dereddening, normalisation), 1 = fold + score of all base periods, and,
  * for every 64th base period of the octave (entries first + 64 j), 2 = its
- * fold launches and 3 = its scoring launch.  ffa_timing_read waits for the
- * recorded events, writes the summed milliseconds of phase p, octave o to
- * ms[p * 64 + o] (cap >= 256 doubles) and the number of recorded intervals
- * to counts[p * 64 + o], then clears the record.  Off by default. */
+ * fold launches and 3 = its scoring launch; base periods folded and scored
+ * in groups (short planes) are timed per group instead, 4 = the group's fold
+ * launches and 5 = its scoring launch, for every group holding one of those
+ * base periods.  ffa_timing_read waits for the recorded events, writes the
+ * summed milliseconds of phase p, octave o to ms[p * 64 + o] and the number
+ * of recorded intervals to counts[p * 64 + o] for every p * 64 + o < cap
+ * (cap >= 256; 384 covers all six phases), then clears the record.  Off by
+ * default. */
 ffa_status ffa_timing_enable(int32_t on);
 
 /* Number of kernel launches (and device copies) the library has enqueued in

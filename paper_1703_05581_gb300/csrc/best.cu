@@ -723,15 +723,16 @@ extern "C" ffa_status ffa2best(const ffa_plan* p, const ffa_record* d_records,
     ffa_status es = ensure_smem((const void*)k_best_select, smem);
     if (es != FFA_OK) return es;
     const int64_t nt = p->n_trials;
+    const int nsm = sm_count();
     k_best_init<<<64, 1024, 0, st>>>(ctl, hist);
-    k_best_spec<<<152 * 8, 256, 0, st>>>(d_records, nt, wa, ck, end_state);
+    k_best_spec<<<nsm * 8, 256, 0, st>>>(d_records, nt, wa, ck, end_state);
     k_best_fix<<<1, 32, 0, st>>>(d_records, nt, wa, 1, ck, end_state, merge, ctl, peaks, hist, fixlist);
-    k_best_tail<<<152 * 8, 256, 0, st>>>(d_records, nt, wa, 1, ck, merge, ctl, peaks, hist);
+    k_best_tail<<<nsm * 8, 256, 0, st>>>(d_records, nt, wa, 1, ck, merge, ctl, peaks, hist);
     for (int level = 0; level < 4; ++level) {  // narrowing passes; no-ops once done
         k_best_plan<<<1, 1024, 0, st>>>(ctl, hist);
-        k_best_refix<<<152, 256, 0, st>>>(ctl, fixlist, peaks, hist);
+        k_best_refix<<<nsm, 256, 0, st>>>(ctl, fixlist, peaks, hist);
         k_best_fix<<<1, 32, 0, st>>>(d_records, nt, wa, 0, ck, end_state, merge, ctl, peaks, hist, fixlist);
-        k_best_tail<<<152 * 8, 256, 0, st>>>(d_records, nt, wa, 0, ck, merge, ctl, peaks, hist);
+        k_best_tail<<<nsm * 8, 256, 0, st>>>(d_records, nt, wa, 0, ck, merge, ctl, peaks, hist);
     }
     k_best_select<<<1, SEL_THREADS, smem, st>>>(d_records, ent, fr_g, fr_c, peaks, ctl, sa, dout);
     FFA_LAUNCH_CHECK("ffa2best kernels");

@@ -17,13 +17,18 @@
 //
 // A CTA owns (block, kappa, column tile): it stages 2^q rows of B + 2^q - 1
 // columns (the halo covers the local shifts) in shared memory, runs the q
-// local stages there (ping-pong buffers) and writes 2^q rows of B columns.
+// local stages in registers (two register-blocked sub-passes) and writes 2^q
+// rows of B columns.  Planes inside a search have a row pitch padded to a
+// multiple of 4 elements, so rows are 16-byte aligned for the staging copies
+// and the 128-bit output stores.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -33,13 +38,18 @@ namespace ffa {
 
 // Base periods folded by one launch: entry i has p0[i] bins, m_data[i] data
 // rows (all share m_rows), its plane at element offset off[i] of the plane
-// buffers, and owns the launch's CTAs [unit0[i], unit0[i + 1]).  A single
-// base period is a group of one.
+// buffers with row pitch ld[i] (>= p0[i]; a multiple of 4 makes every row
+// 16-byte aligned), and owns the launch's CTAs [unit0[i], unit0[i + 1]).  A
+// single base period is a group of one.  The first pass reads the series
+// itself: row g of entry i is src[i][g * p0[i] ...], densely packed (entries
+// of a batch read their own series).
 struct FoldGroup {
     int32_t n;
+    const void* src[FOLD_GROUP_MAX];
     int64_t p0[FOLD_GROUP_MAX];
     int64_t m_data[FOLD_GROUP_MAX];
     int64_t off[FOLD_GROUP_MAX];
+    int64_t ld[FOLD_GROUP_MAX];
     int64_t unit0[FOLD_GROUP_MAX + 1];
 };
 
@@ -61,158 +71,101 @@ struct FoldIn<float> { using type = float; };
 template <>
 struct FoldIn<int32_t> { using type = int8_t; };
 
-// Asynchronous 4-byte global -> shared copy (cp.async): a lane issues all of
-// its copies for a tile without waiting, then waits once (cp_async_wait).
+// Asynchronous global -> shared copies (cp.async): a lane issues all of its
+// copies for a tile without waiting, then waits once (cp_async_wait).  The
+// 16-byte form bypasses L1 (each element is read by one tile only, apart from
+// the halo, which the next tile finds in L2).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-template <class T, class S>
-__device__ __forceinline__ void put_async(T* dst, const S* src) {
-    if constexpr (sizeof(T) == sizeof(S)) cp_async4(dst, src);
-    else *dst = (T)*src;  // int8 series into int32 rows: converted through registers
-}
-
 // Stage `wt` cyclic columns of a row starting at column `base` (< p0) into
-// shared memory: at most one wrap when wt <= p0, so the segment is two
-// contiguous runs.  Same-width rows are copied with cp.async (the caller
-// waits with cp_async_wait before its barrier), so every row of a tile is in
-// flight at once.
+// shared memory (one warp per row); returns the element offset (0..3) of
+// logical column 0 in rowp (16-byte aligned).  A segment that does not wrap
+// is copied as whole 16-byte chunks from its aligned-down start, so the
+// offset is its misalignment; the chunk holding the segment's last element
+// ends within that element's 16-byte block, so nothing outside it is read.
+// A wrapping segment (or a row shorter than the segment) is copied element
+// by element at offset 0, int8 rows are widened to int32 through registers,
+// and rows at or beyond m_data (live == false) are zero.
 template <class T, class S>
-__device__ __forceinline__ void stage_row(T* __restrict__ rowp, const S* __restrict__ src, int64_t base,
-                                          int64_t p0, int wt, bool live, int lane) {
+__device__ __forceinline__ int stage_row(T* __restrict__ rowp, const S* __restrict__ src, int64_t base,
+                                         int64_t p0, int wt, bool live, int lane) {
     if (!live) {
-        for (int x = lane; x < wt; x += 32) rowp[x] = (T)0;
-        return;
+        for (int x = 4 * lane; x < wt; x += 128) *reinterpret_cast<int4*>(rowp + x) = make_int4(0, 0, 0, 0);
+        return 0;
     }
-    if (wt <= p0) {
-        const int n1 = (int)((p0 - base) < wt ? (p0 - base) : wt);  // columns before the wrap
-        const S* a = src + base;
-#pragma unroll 4
-        for (int x = lane; x < n1; x += 32) put_async(rowp + x, a + x);
-#pragma unroll 4
-        for (int x = n1 + lane; x < wt; x += 32) put_async(rowp + x, src + (x - n1));
+    if constexpr (sizeof(T) == sizeof(S)) {
+        if (base + wt <= p0) {
+            const S* g = src + base;
+            const int a = (int)(((uintptr_t)g >> 2) & 3);
+            const S* g0 = g - a;
+            const int nc = (wt + a + 3) >> 2;
+            for (int k = lane; k < nc; k += 32) cp_async16(rowp + 4 * k, g0 + 4 * k);
+            return a;
+        }
+        if (wt <= p0) {
+            const int n1 = (int)(p0 - base);  // columns before the wrap
+            const S* a = src + base;
+            for (int x = lane; x < n1; x += 32) cp_async4(rowp + x, a + x);
+            for (int x = n1 + lane; x < wt; x += 32) cp_async4(rowp + x, src + (x - n1));
+            return 0;
+        }
+        int64_t col = base + lane;
+        while (col >= p0) col -= p0;
+        for (int x = lane; x < wt; x += 32) {
+            cp_async4(rowp + x, src + col);
+            col += 32;
+            while (col >= p0) col -= p0;
+        }
+        return 0;
     } else {
         int64_t col = base + lane;
         while (col >= p0) col -= p0;
         for (int x = lane; x < wt; x += 32) {
-            put_async(rowp + x, src + col);
+            rowp[x] = (T)src[col];
             col += 32;
             while (col >= p0) col -= p0;
         }
+        return 0;
     }
 }
 
 // ---------------------------------------------------------------------------
-// One pass of q <= 5 stages.  A CTA owns (block, kappa, column tile): it
-// stages 2^q rows of B + 2^q - 1 columns in shared memory (row u starting at
-// column c + kappa*u, cyclically), runs the q local stages with one warp per
-// row (ping-pong buffers, conflict-free contiguous accesses) and writes 2^q
-// rows of B columns.
-// ---------------------------------------------------------------------------
-constexpr int FP_THREADS = 256;
-constexpr int FP_B = 256;
-
-template <class T, bool FIRST>
-__global__ void __launch_bounds__(FP_THREADS) k_fold_pass(const void* __restrict__ src_v,
-                                                          T* __restrict__ dst_all, const FoldGroup fg,
-                                                          int s, int q) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int rows = 1 << q;
-    const int wt = FP_B + rows - 1;
-    T* buf0 = reinterpret_cast<T*>(smem_raw);
-    T* buf1 = buf0 + rows * wt;
-    const int ei = group_entry(fg, blockIdx.x);
-    const int64_t p0 = fg.p0[ei], m_data = fg.m_data[ei];
-    const int64_t n_ct = (p0 + FP_B - 1) / FP_B;
-    T* __restrict__ dst = dst_all + fg.off[ei];
-    if (!FIRST) src_v = (const T*)src_v + fg.off[ei];
-    const int64_t unit = blockIdx.x - fg.unit0[ei];
-    const int64_t ct = unit % n_ct;
-    const int64_t rest = unit / n_ct;
-    const int64_t kappa = rest & ((1ll << s) - 1);
-    const int64_t blk = rest >> s;
-    const int64_t c = ct * FP_B;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int NW = FP_THREADS / 32;
-
-    const int64_t kmod = kappa % p0;
-    for (int u = warp; u < rows; u += NW) {
-        const int64_t g = blk * rows + u;  // group index at level s
-        int64_t base = c + (kmod * (u % p0)) % p0;
-        if (base >= p0) base -= p0;
-        if (FIRST)
-            stage_row(buf0 + u * wt, (const typename FoldIn<T>::type*)src_v + g * p0, base, p0, wt,
-                      g < m_data, lane);
-        else
-            stage_row(buf0 + u * wt, (const T*)src_v + ((g << s) + kappa) * p0, base, p0, wt, true, lane);
-    }
-    cp_async_wait();
-    __syncthreads();
-    T* in = buf0;
-    T* out = buf1;
-    for (int t = 1; t <= q; ++t) {
-        const int half = 1 << (t - 1);
-        const int width = wt - ((1 << t) - 1);
-        for (int r = warp; r < rows; r += NW) {
-            const int gb = r & ~((1 << t) - 1);
-            const int v = r - gb;
-            const T* h = in + (gb + (v >> 1)) * wt;
-            const T* tl = in + (gb + half + (v >> 1)) * wt + ((v + 1) >> 1);
-            T* o = out + r * wt;
-            for (int x = lane; x < width; x += 32) o[x] = h[x] + tl[x];
-        }
-        __syncthreads();
-        T* tmp = in;
-        in = out;
-        out = tmp;
-    }
-    const int64_t out_row0 = (blk << (s + q)) + (kappa << q);
-    const int64_t ncols = (c + FP_B <= p0) ? FP_B : p0 - c;
-    for (int v = warp; v < rows; v += NW) {
-        T* d = dst + (out_row0 + v) * p0 + c;
-        const T* sv = in + v * wt;
-        for (int x = lane; x < ncols; x += 32) d[x] = sv[x];
-    }
-}
-
-// Split m stages into passes of at most `qmax`, as evenly as possible.
-static int split_passes(int m, int qmax, int* qs) {
-    if (m == 0) return 0;
-    int np = (m + qmax - 1) / qmax;
-    for (int i = 0; i < np; ++i) qs[i] = m / np + (i < m % np ? 1 : 0);
-    return np;
-}
-
-// ---------------------------------------------------------------------------
-// Register-blocked pass (q = Q1 + Q2 <= 5 stages).  After staging the tile
-// as above, each thread takes 4 consecutive columns of one group of 2^Q1 rows,
-// loads them with aligned 128-bit shared-memory reads, applies Q1 stages in
-// registers (compile-time shifts) and stores its 2^Q1 partial trials already
-// shifted left by kappa1*u2, the column offset at which the second sub-pass
-// reads them; the second sub-pass then reads 128-bit aligned as well, applies
-// the remaining Q2 stages and writes the tile's output rows to global memory.
-// Neighbouring threads take neighbouring columns: conflict-free 16-byte reads.
+// The FFA of R = 2^QQ rows on W = 4 + R - 1 consecutive columns held in
+// registers (compile-time shifts): out[v][0..3] is trial v at the first four
+// columns.  load() reads a row's W values starting at element offset `off`
+// (0..3) of a 16-byte aligned pointer: 128-bit loads, then two branch-free
+// selects per value.
 // ---------------------------------------------------------------------------
 template <class T, int QQ>
-struct RegStages {
+struct RegFFA {
     static constexpr int R = 1 << QQ;
-    static constexpr int W = 4 + R - 1;      // columns needed for 4 outputs
-    static constexpr int NV = (W + 3) / 4;   // 128-bit loads per row
-    // rows: R pointers (16-byte aligned) into shared memory; out[v][0..3]
-    static __device__ __forceinline__ void run(const T* const* rowp, T (&out)[R][4]) {
-        T a[R][NV * 4];
+    static constexpr int W = 4 + R - 1;
+    static constexpr int NV = (W + 6) / 4;  // 128-bit loads covering W values at any offset
+    static __device__ __forceinline__ void load(const T* p, int off, T (&a)[W]) {
+        T r[4 * NV];
 #pragma unroll
-        for (int u = 0; u < R; ++u)
+        for (int k = 0; k < NV; ++k)
+            *reinterpret_cast<int4*>(&r[4 * k]) = *reinterpret_cast<const int4*>(p + 4 * k);
+        const bool b0 = (off & 1) != 0, b1 = (off & 2) != 0;
+        T t[W + 2];
 #pragma unroll
-            for (int k = 0; k < NV; ++k)
-                *reinterpret_cast<int4*>(&a[u][4 * k]) = *reinterpret_cast<const int4*>(rowp[u] + 4 * k);
+        for (int k = 0; k < W + 2; ++k) t[k] = b0 ? r[k + 1] : r[k];
+#pragma unroll
+        for (int k = 0; k < W; ++k) a[k] = b1 ? t[k + 2] : t[k];
+    }
+    static __device__ __forceinline__ void run(T (&a)[R][W], T (&out)[R][4]) {
 #pragma unroll
         for (int t = 1; t <= QQ; ++t) {
             const int g = 1 << t, half = g >> 1;
-            T b[R][NV * 4];
+            T b[R][W];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int gb = r & ~(g - 1), v = r - gb;
@@ -233,113 +186,158 @@ struct RegStages {
     }
 };
 
-constexpr int F4_THREADS = 256;
-constexpr int F4_B = 256;
-__host__ __device__ constexpr int f4_wa(int q) { return ((F4_B + (1 << q) - 1 + 3) & ~3) + 8; }
-__host__ __device__ constexpr int f4_wb(int q, int q1) { return ((F4_B + (1 << q) - (1 << q1) + 3) & ~3) + 8; }
+template <class T>
+__device__ __forceinline__ int as_bits(T v) {
+    if constexpr (sizeof(T) == 4 && !std::is_integral<T>::value) return __float_as_int(v);
+    else return (int)v;
+}
+
+// Four consecutive outputs to global memory: one 128-bit store when the row
+// is 16-byte aligned (vec), else element stores up to `left` columns.
+template <class T>
+__device__ __forceinline__ void store4(T* d, const T (&v)[4], int64_t left, bool vec) {
+    if (vec) {
+        *reinterpret_cast<int4*>(d) = make_int4(as_bits(v[0]), as_bits(v[1]), as_bits(v[2]), as_bits(v[3]));
+    } else {
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+            if (x < left) d[x] = v[x];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One pass of q = Q1 + Q2 <= 6 stages.  A CTA owns (block, kappa, column
+// tile of B columns): it stages 2^q input rows of B + 2^q - 1 columns, row u
+// starting at column c + kappa*u (cyclically), in shared memory.  Sub-pass 1:
+// each thread takes 4 consecutive columns of a group of 2^Q1 rows, applies
+// Q1 stages in registers and stores the group's 2^Q1 partial trials,
+// unshifted, with 128-bit stores.  Sub-pass 2: for trial k1 of sub-pass 1,
+// input row u2 of the last Q2 stages is read at column offset k1*u2 (the
+// shift that the unrolled recursion assigns it), Q2 stages in registers, and
+// the tile's output rows go to global memory (128-bit stores on a padded
+// pitch).  Tiles are B = 256 columns up to 5 stages and 128 for 6 (64 rows),
+// so two CTAs fit an SM.
+// ---------------------------------------------------------------------------
+constexpr int FK_THREADS = 256;
+__host__ __device__ constexpr int fk_b(int q) { return q >= 6 ? 128 : 256; }
+__host__ __device__ constexpr int fk_r4(int x) { return (x + 3) & ~3; }
+__host__ __device__ constexpr int fk_max(int a, int b) { return a > b ? a : b; }
+__host__ __device__ constexpr int fk_wt(int q) { return fk_b(q) + (1 << q) - 1; }                  // staged columns
+__host__ __device__ constexpr int fk_w1(int q, int q1) { return fk_b(q) + (1 << q) - (1 << q1); }  // valid after sub-pass 1
+// Row widths (elements) of the two shared buffers: room for the staging
+// copies and for every 128-bit load of the two sub-passes.
+__host__ __device__ constexpr int fk_wa(int q, int q1) {
+    return fk_max(fk_r4(fk_wt(q) + 3), 4 * ((fk_w1(q, q1) + 3) / 4 - 1) + 4 * ((4 + (1 << q1) - 1 + 6) / 4));
+}
+__host__ __device__ constexpr int fk_wb(int q, int q1) {
+    return fk_max(fk_r4(fk_w1(q, q1)), (fk_b(q) - 4) + 4 * ((((1 << q1) - 1) * ((1 << (q - q1)) - 1)) / 4) +
+                                           4 * ((4 + (1 << (q - q1)) - 1 + 6) / 4));
+}
 
 template <class T, bool FIRST, int Q1, int Q2>
-__global__ void __launch_bounds__(F4_THREADS, 2) k_fold_reg(const void* __restrict__ src_v,
-                                                           T* __restrict__ dst_all, const FoldGroup fg,
-                                                           int s) {
+__global__ void __launch_bounds__(FK_THREADS, 2) k_fold(const void* __restrict__ src_v, T* __restrict__ dst_all,
+                                                       const FoldGroup fg, int s) {
     constexpr int q = Q1 + Q2;
     constexpr int rows = 1 << q;
     constexpr int R1 = 1 << Q1, R2 = 1 << Q2;
-    constexpr int WA = f4_wa(q), WB = f4_wb(q, Q1);
-    constexpr int W1 = F4_B + rows - R1;  // valid columns after the first sub-pass
+    constexpr int B = fk_b(q), WT = fk_wt(q), W1 = fk_w1(q, Q1);
+    constexpr int WA = fk_wa(q, Q1), WB = fk_wb(q, Q1);
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int off_a[rows];
     T* bufA = reinterpret_cast<T*>(smem_raw);
     T* bufB = bufA + rows * WA;
 
     const int ei = group_entry(fg, blockIdx.x);
-    const int64_t p0 = fg.p0[ei], m_data = fg.m_data[ei];
-    const int64_t n_ct = (p0 + F4_B - 1) / F4_B;
+    const int64_t p0 = fg.p0[ei], m_data = fg.m_data[ei], ld = fg.ld[ei];
+    const int64_t n_ct = (p0 + B - 1) / B;
     T* __restrict__ dst = dst_all + fg.off[ei];
-    if (!FIRST) src_v = (const T*)src_v + fg.off[ei];
     const int64_t unit = blockIdx.x - fg.unit0[ei];
     const int64_t ct = unit % n_ct;
     const int64_t rest = unit / n_ct;
     const int64_t kappa = rest & ((1ll << s) - 1);
     const int64_t blk = rest >> s;
-    const int64_t c = ct * F4_B;
+    const int64_t c = ct * B;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int NW = F4_THREADS / 32;
-    constexpr int WT = F4_B + rows - 1;  // staged columns
+    constexpr int NW = FK_THREADS / 32;
 
     const int64_t kmod = kappa % p0;
     for (int u = warp; u < rows; u += NW) {
         const int64_t g = blk * rows + u;
         int64_t base = c + (kmod * (u % p0)) % p0;
         if (base >= p0) base -= p0;
+        int a;
         if (FIRST)
-            stage_row(bufA + u * WA, (const typename FoldIn<T>::type*)src_v + g * p0, base, p0, WT,
-                      g < m_data, lane);
+            a = stage_row(bufA + u * WA, (const typename FoldIn<T>::type*)fg.src[ei] + g * p0, base, p0, WT,
+                          g < m_data, lane);
         else
-            stage_row(bufA + u * WA, (const T*)src_v + ((g << s) + kappa) * p0, base, p0, WT, true, lane);
+            a = stage_row(bufA + u * WA, (const T*)src_v + fg.off[ei] + ((g << s) + kappa) * ld, base, p0, WT, true,
+                          lane);
+        if (lane == 0) off_a[u] = a;
     }
     cp_async_wait();
     __syncthreads();
     const int64_t grow0 = (blk << (s + q)) + (kappa << q);
-    const int64_t ncols = (c + F4_B <= p0) ? F4_B : p0 - c;
+    const int64_t ncols = (c + B <= p0) ? B : p0 - c;
+    const bool vec = (ld & 3) == 0 && ((uintptr_t)dst & 15) == 0;
 
-    // first sub-pass: groups of R1 consecutive rows
+    // sub-pass 1: groups of R1 consecutive rows
     {
+        constexpr int W = RegFFA<T, Q1>::W;
         constexpr int nstrips = (W1 + 3) / 4;
         constexpr int items = (rows / R1) * nstrips;
-        for (int it = threadIdx.x; it < items; it += F4_THREADS) {
+        for (int it = threadIdx.x; it < items; it += FK_THREADS) {
             const int strip = it % nstrips, g = it / nstrips;
             const int x0 = 4 * strip;
-            const T* rp[R1];
+            T a[R1][W];
 #pragma unroll
-            for (int u = 0; u < R1; ++u) rp[u] = bufA + (g * R1 + u) * WA + x0;
+            for (int u = 0; u < R1; ++u) RegFFA<T, Q1>::load(bufA + (g * R1 + u) * WA + x0, off_a[g * R1 + u], a[u]);
             T out[R1][4];
-            RegStages<T, Q1>::run(rp, out);
+            RegFFA<T, Q1>::run(a, out);
             if (Q2 == 0) {
+                if (x0 < ncols) {
 #pragma unroll
-                for (int v = 0; v < R1; ++v) {
-                    T* d = dst + (grow0 + v) * p0 + c + x0;
-#pragma unroll
-                    for (int x = 0; x < 4; ++x)
-                        if (x0 + x < ncols) d[x] = out[v][x];
+                    for (int v = 0; v < R1; ++v) store4(dst + (grow0 + v) * ld + c + x0, out[v], ncols - x0, vec);
                 }
             } else {
-                // group g is input row u2 = g of the second sub-pass; trial v of it is
-                // read at column offset v*u2: store it shifted left by that much
-                const int u2 = g;
+                // group g is input row u2 = g of sub-pass 2
 #pragma unroll
-                for (int v = 0; v < R1; ++v) {
-                    T* d = bufB + (v * R2 + u2) * WB;
-                    const int sh = v * u2;
-#pragma unroll
-                    for (int x = 0; x < 4; ++x) {
-                        const int xx = x0 + x - sh;
-                        if (xx >= 0 && x0 + x < W1) d[xx] = out[v][x];
-                    }
-                }
+                for (int v = 0; v < R1; ++v)
+                    *reinterpret_cast<int4*>(bufB + (v * R2 + g) * WB + x0) =
+                        make_int4(as_bits(out[v][0]), as_bits(out[v][1]), as_bits(out[v][2]), as_bits(out[v][3]));
             }
         }
     }
     if (Q2 > 0) {
         __syncthreads();
-        constexpr int nstrips = F4_B / 4;
+        constexpr int W = RegFFA<T, Q2>::W;
+        constexpr int nstrips = B / 4;
         constexpr int items = R1 * nstrips;
-        for (int it = threadIdx.x; it < items; it += F4_THREADS) {
+        for (int it = threadIdx.x; it < items; it += FK_THREADS) {
             const int strip = it % nstrips, k1 = it / nstrips;
             const int x0 = 4 * strip;
-            const T* rp[R2];
+            T a[R2][W];
 #pragma unroll
-            for (int u = 0; u < R2; ++u) rp[u] = bufB + (k1 * R2 + u) * WB + x0;
+            for (int u = 0; u < R2; ++u) {
+                const int sh = k1 * u;
+                RegFFA<T, Q2>::load(bufB + (k1 * R2 + u) * WB + x0 + (sh & ~3), sh & 3, a[u]);
+            }
             T out[R2][4];
-            RegStages<T, Q2>::run(rp, out);
+            RegFFA<T, Q2>::run(a, out);
+            if (x0 < ncols) {
 #pragma unroll
-            for (int v = 0; v < R2; ++v) {
-                T* d = dst + (grow0 + k1 * R2 + v) * p0 + c + x0;
-#pragma unroll
-                for (int x = 0; x < 4; ++x)
-                    if (x0 + x < ncols) d[x] = out[v][x];
+                for (int v = 0; v < R2; ++v)
+                    store4(dst + (grow0 + k1 * R2 + v) * ld + c + x0, out[v], ncols - x0, vec);
             }
         }
     }
+}
+
+// Split m stages into passes of at most `qmax`, as evenly as possible.
+static int split_passes(int m, int qmax, int* qs) {
+    if (m == 0) return 0;
+    int np = (m + qmax - 1) / qmax;
+    for (int i = 0; i < np; ++i) qs[i] = m / np + (i < m % np ? 1 : 0);
+    return np;
 }
 
 // Fill the group's CTA ranges for a pass whose CTAs cover `rows` output rows
@@ -355,16 +353,17 @@ static int64_t group_units(FoldGroup& fg, int64_t m_rows, int rows, int tile) {
 }
 
 template <class T, bool FIRST, int Q1, int Q2>
-static ffa_status launch_reg(const void* src, T* dst, FoldGroup& fg, int64_t m_rows, int s, cudaStream_t st) {
+static ffa_status launch_k(const void* src, T* dst, FoldGroup& fg, int64_t m_rows, int s, cudaStream_t st) {
     constexpr int q = Q1 + Q2;
     constexpr int rows = 1 << q;
-    const size_t smem = sizeof(T) * ((size_t)rows * f4_wa(q) + (Q2 > 0 ? (size_t)rows * f4_wb(q, Q1) : 0));
-    ffa_status es = ensure_smem((const void*)k_fold_reg<T, FIRST, Q1, Q2>, smem);
+    const size_t smem = sizeof(T) * ((size_t)rows * fk_wa(q, Q1) + (Q2 > 0 ? (size_t)rows * fk_wb(q, Q1) : 0));
+    ffa_status es = ensure_smem((const void*)k_fold<T, FIRST, Q1, Q2>, smem);
     if (es != FFA_OK) return es;
-    const int64_t units = group_units(fg, m_rows, rows, F4_B);
+    const int64_t units = group_units(fg, m_rows, rows, fk_b(q));
     if (units <= 0) return FFA_OK;
-    k_fold_reg<T, FIRST, Q1, Q2><<<(unsigned)units, F4_THREADS, smem, st>>>(src, dst, fg, s);
-    FFA_LAUNCH_CHECK("k_fold_reg");
+    if (units > INT32_MAX) return fail(FFA_ERR_UNSUPPORTED, "fold: plane too large for one launch");
+    k_fold<T, FIRST, Q1, Q2><<<(unsigned)units, FK_THREADS, smem, st>>>(src, dst, fg, s);
+    FFA_LAUNCH_CHECK("k_fold");
     count_launch();
     return FFA_OK;
 }
@@ -373,23 +372,16 @@ template <class T, bool FIRST>
 static ffa_status pass_q(int q, const void* src, T* dst, FoldGroup& fg, int64_t m_rows, int s,
                          cudaStream_t st) {
     switch (q) {
-        case 1: return launch_reg<T, FIRST, 1, 0>(src, dst, fg, m_rows, s, st);
-        case 2: return launch_reg<T, FIRST, 2, 0>(src, dst, fg, m_rows, s, st);
-        case 3: return launch_reg<T, FIRST, 3, 0>(src, dst, fg, m_rows, s, st);
-        case 4: return launch_reg<T, FIRST, 2, 2>(src, dst, fg, m_rows, s, st);
-        case 5: return launch_reg<T, FIRST, 3, 2>(src, dst, fg, m_rows, s, st);
+        case 0: return launch_k<T, FIRST, 0, 0>(src, dst, fg, m_rows, s, st);
+        case 1: return launch_k<T, FIRST, 1, 0>(src, dst, fg, m_rows, s, st);
+        case 2: return launch_k<T, FIRST, 2, 0>(src, dst, fg, m_rows, s, st);
+        case 3: return launch_k<T, FIRST, 3, 0>(src, dst, fg, m_rows, s, st);
+        case 4: return launch_k<T, FIRST, 2, 2>(src, dst, fg, m_rows, s, st);
+        case 5: return launch_k<T, FIRST, 3, 2>(src, dst, fg, m_rows, s, st);
+        case 6: return launch_k<T, FIRST, 3, 3>(src, dst, fg, m_rows, s, st);
         default: break;
     }
-    const int rows = 1 << q;
-    const size_t smem = 2 * sizeof(T) * (size_t)rows * (FP_B + rows - 1);
-    ffa_status es = ensure_smem((const void*)k_fold_pass<T, FIRST>, smem);
-    if (es != FFA_OK) return es;
-    const int64_t units = group_units(fg, m_rows, rows, FP_B);
-    if (units <= 0) return FFA_OK;
-    k_fold_pass<T, FIRST><<<(unsigned)units, FP_THREADS, smem, st>>>(src, dst, fg, s, q);
-    FFA_LAUNCH_CHECK("k_fold_pass");
-    count_launch();
-    return FFA_OK;
+    return fail(FFA_ERR_ARG, "fold: at most 6 stages per pass");
 }
 
 template <class T>
@@ -420,12 +412,12 @@ static ffa_status fold_impl(const void* d_z, FoldGroup& fg, int64_t m_rows, int 
 // Stages per pass, tuned.  Any split of the stages into passes gives the
 // same add tree (bit-identical planes); only the time differs.  The cache
 // maps (device, precision, stages, floor(log2 p0)) to the fastest maximum
-// pass depth measured by tune_fold; untuned shapes use 5.
+// pass depth measured by tune_fold; untuned shapes use 6.
 // ---------------------------------------------------------------------------
 namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, int> g_tune;
-constexpr int QMAX_DEFAULT = 5;
+constexpr int QMAX_DEFAULT = 6;
 
 int log2i(int64_t v) {
     int r = 0;
@@ -450,31 +442,33 @@ static ffa_status fold_group(const void* d_z, int32_t precision, FoldGroup& fg, 
 }
 
 ffa_status fold_with(const void* d_z, int32_t precision, int64_t p0, int64_t m_data, int64_t m_rows,
-                     int stages, void* d_plane, void* d_tmp, cudaStream_t st, int qmax) {
+                     int stages, int64_t ld, void* d_plane, void* d_tmp, cudaStream_t st, int qmax) {
     FoldGroup fg;
     fg.n = 1;
     fg.p0[0] = p0;
     fg.m_data[0] = m_data;
     fg.off[0] = 0;
+    fg.ld[0] = ld;
+    fg.src[0] = d_z;
     return fold_group(d_z, precision, fg, m_rows, stages, d_plane, d_tmp, st, qmax);
 }
 
-// Time each maximum pass depth 3..5 on one shape (CUDA events, best of 2
+// Time each maximum pass depth 3..6 on one shape (CUDA events, best of 2
 // after a warm-up) and cache the fastest.  The planes are scratch.
 ffa_status tune_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data, int64_t m_rows,
-                     int stages, void* d_plane, void* d_tmp, cudaStream_t st, int* best_q) {
+                     int stages, int64_t ld, void* d_plane, void* d_tmp, cudaStream_t st, int* best_q) {
     cudaEvent_t e0, e1;
     FFA_CUDA_TRY(cudaEventCreate(&e0));
     FFA_CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
     int bq = QMAX_DEFAULT;
     ffa_status s = FFA_OK;
-    for (int q = 3; q <= 5 && s == FFA_OK; ++q) {
-        s = fold_with(d_z, precision, p0, m_data, m_rows, stages, d_plane, d_tmp, st, q);  // warm-up
+    for (int q = 3; q <= 6 && s == FFA_OK; ++q) {
+        s = fold_with(d_z, precision, p0, m_data, m_rows, stages, ld, d_plane, d_tmp, st, q);  // warm-up
         float t_q = 1e30f;
         for (int rep = 0; rep < 2 && s == FFA_OK; ++rep) {
             cudaEventRecord(e0, st);
-            s = fold_with(d_z, precision, p0, m_data, m_rows, stages, d_plane, d_tmp, st, q);
+            s = fold_with(d_z, precision, p0, m_data, m_rows, stages, ld, d_plane, d_tmp, st, q);
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) s = cuda_fail(cudaGetLastError(), "tune_fold");
             float ms = 0.0f;
@@ -501,7 +495,7 @@ ffa_status tune_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_d
 
 ffa_status launch_fold_group(const void* d_z, int32_t precision, int n, const int64_t* p0, const int64_t* m_data,
                              const int64_t* off, int64_t m_rows, int stages, void* d_plane, void* d_tmp,
-                             cudaStream_t st) {
+                             cudaStream_t st, const void* const* z) {
     if (n < 1 || n > FOLD_GROUP_MAX) return fail(FFA_ERR_ARG, "fold group: 1..FOLD_GROUP_MAX base periods");
     FoldGroup fg;
     fg.n = n;
@@ -509,6 +503,8 @@ ffa_status launch_fold_group(const void* d_z, int32_t precision, int n, const in
         fg.p0[i] = p0[i];
         fg.m_data[i] = m_data[i];
         fg.off[i] = off[i];
+        fg.ld[i] = plane_pitch(p0[i]);
+        fg.src[i] = z ? z[i] : d_z;
     }
     return fold_group(d_z, precision, fg, m_rows, stages, d_plane, d_tmp, st,
                       tuned_qmax(precision, stages, p0[n - 1]));
@@ -518,11 +514,11 @@ ffa_status launch_fold_group(const void* d_z, int32_t precision, int n, const in
 // fewer stages the plane holds, per group of 2^stages rows, its partial
 // trials (row g * 2^stages + kappa); zero stages copy the (zero-padded) rows.
 ffa_status launch_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
-                       int64_t m_rows, int stages, void* d_plane, void* d_tmp, cudaStream_t st) {
+                       int64_t m_rows, int stages, int64_t ld, void* d_plane, void* d_tmp, cudaStream_t st) {
     int m = 0;
     while ((1ll << m) < m_rows) ++m;
     if (stages < 0 || stages > m) stages = m;
-    return fold_with(d_z, precision, p0, m_data, m_rows, stages, d_plane, d_tmp, st,
+    return fold_with(d_z, precision, p0, m_data, m_rows, stages, ld, d_plane, d_tmp, st,
                      tuned_qmax(precision, stages, p0));
 }
 
@@ -536,8 +532,46 @@ namespace {
 // in the module image, so every GPU that loads the library holds it.
 static __device__ __align__(256) float g_fold_scratch[FFA_NOALLOC_FOLD_MAX_ELEMS];
 
+// The array's device address is looked up once per device and context: a
+// cudaDeviceReset (or any re-creation of the primary context) reloads the
+// module, so the address is looked up again when the current context's
+// unique id changes.  The driver calls come through the runtime's entry
+// point query, so the library still links only against the runtime.
+typedef CUresult (*ctx_get_current_t)(CUcontext*);
+typedef CUresult (*ctx_get_id_t)(CUcontext, unsigned long long*);
+
 std::mutex g_scratch_mu;
-void* g_scratch_ptr[64] = {};
+struct ScratchSlot {
+    void* ptr = nullptr;
+    unsigned long long ctx_id = 0;
+    bool has_id = false;
+};
+ScratchSlot g_scratch[64];
+
+// Unique id of the calling thread's current context; false if none is
+// current yet or the driver does not offer the query.
+bool current_ctx_id(unsigned long long* id) {
+    static ctx_get_current_t get_cur = nullptr;
+    static ctx_get_id_t get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            get_cur = (ctx_get_current_t)f1;
+            get_id = (ctx_get_id_t)f2;
+        }
+    }
+    if (!get_cur || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 }  // namespace
 
 extern "C" ffa_status ffa_fold_noalloc(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
@@ -548,7 +582,8 @@ extern "C" ffa_status ffa_fold_noalloc(const void* d_z, int32_t precision, int64
     if (precision != FFA_FOLD_F32 && precision != FFA_FOLD_I8)
         return fail(FFA_ERR_ARG, "fold_noalloc: bad precision");
     if (!d_z || !d_plane) return fail(FFA_ERR_ARG, "fold_noalloc: null buffer");
-    if (m_rows * p0 > (int64_t)FFA_NOALLOC_FOLD_MAX_ELEMS)
+    // m_rows >= 1 here; the division form cannot overflow
+    if (p0 > (int64_t)FFA_NOALLOC_FOLD_MAX_ELEMS / m_rows)
         return fail(FFA_ERR_UNSUPPORTED,
                     "fold_noalloc: m_rows * p0 exceeds FFA_NOALLOC_FOLD_MAX_ELEMS (the fixed scratch)");
     int dev = 0;
@@ -556,16 +591,22 @@ extern "C" ffa_status ffa_fold_noalloc(const void* d_z, int32_t precision, int64
     if (dev < 0 || dev >= 64) return fail(FFA_ERR_UNSUPPORTED, "fold_noalloc: device index >= 64");
     void* scratch;
     {
-        // set-up once per device, with that device current: the device address of
-        // the array (its host-side name is only a stand-in, not a device address)
+        // set-up once per device and context, with that device current: the
+        // device address of the array (its host-side name is only a stand-in,
+        // not a device address)
         std::lock_guard<std::mutex> lk(g_scratch_mu);
-        if (!g_scratch_ptr[dev]) {
+        ScratchSlot& sl = g_scratch[dev];
+        unsigned long long id = 0;
+        const bool has_id = current_ctx_id(&id);
+        if (!sl.ptr || !has_id || !sl.has_id || id != sl.ctx_id) {
             void* ptr = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&ptr, g_fold_scratch);
             if (e != cudaSuccess || !ptr) return cuda_fail(e, "fold_noalloc: cudaGetSymbolAddress");
-            g_scratch_ptr[dev] = ptr;
+            sl.ptr = ptr;
+            // the lookup makes the primary context current if none was
+            sl.has_id = current_ctx_id(&sl.ctx_id);
         }
-        scratch = g_scratch_ptr[dev];
+        scratch = sl.ptr;
     }
-    return launch_fold(d_z, precision, p0, m_data, m_rows, -1, d_plane, scratch, as_stream(stream));
+    return launch_fold(d_z, precision, p0, m_data, m_rows, -1, p0, d_plane, scratch, as_stream(stream));
 }

@@ -14,7 +14,7 @@ namespace ffa {
 namespace {
 
 __global__ void __launch_bounds__(256) k_persist(const int32_t* __restrict__ plane, int64_t m_rows,
-                                                 int64_t p0, const ffa_record* __restrict__ rec,
+                                                 int64_t p0, int64_t ld, const ffa_record* __restrict__ rec,
                                                  uint32_t* __restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -22,8 +22,8 @@ __global__ void __launch_bounds__(256) k_persist(const int32_t* __restrict__ pla
     for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < m_rows; k += n_warps) {
         const ffa_record r = rec[k];
         const int64_t w = r.width, ph = r.phase;
-        const int32_t* h = m_rows > 1 ? plane + (k >> 1) * p0 : plane;
-        const int32_t* t = m_rows > 1 ? plane + (half + (k >> 1)) * p0 : nullptr;
+        const int32_t* h = m_rows > 1 ? plane + (k >> 1) * ld : plane;
+        const int32_t* t = m_rows > 1 ? plane + (half + (k >> 1)) * ld : nullptr;
         const int64_t sh = ((k + 1) >> 1) % p0;
         uint32_t acc = 0;
         for (int64_t i = lane; i < w; i += 32) {
@@ -43,12 +43,12 @@ __global__ void __launch_bounds__(256) k_persist(const int32_t* __restrict__ pla
 
 }  // namespace
 
-ffa_status launch_persist(const int32_t* d_bplane, int64_t m_rows, int64_t p0,
+ffa_status launch_persist(const int32_t* d_bplane, int64_t m_rows, int64_t p0, int64_t ld,
                           const ffa_record* d_rec, uint32_t* d_persist, cudaStream_t st) {
     if (m_rows <= 0) return FFA_OK;
     const int64_t blocks = (m_rows * 32 + 255) / 256;
-    const int grid = (int)(blocks < 152 * 8 ? blocks : 152 * 8);
-    k_persist<<<grid, 256, 0, st>>>(d_bplane, m_rows, p0, d_rec, d_persist);
+    const int grid = (int)(blocks < sm_count() * 8 ? blocks : sm_count() * 8);
+    k_persist<<<grid, 256, 0, st>>>(d_bplane, m_rows, p0, ld, d_rec, d_persist);
     FFA_LAUNCH_CHECK("k_persist");
     count_launch(1);
     return FFA_OK;

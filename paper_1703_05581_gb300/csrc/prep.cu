@@ -51,7 +51,7 @@ __global__ void k_downsample2(const double* __restrict__ x, int64_t m, double* _
 
 static int grid_for(int64_t m, int block) {
     int64_t g = (m + block - 1) / block;
-    int64_t cap = 152 * 16;
+    int64_t cap = (int64_t)sm_count() * 16;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     return (int)g;

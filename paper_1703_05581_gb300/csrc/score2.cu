@@ -550,13 +550,17 @@ __device__ __forceinline__ T width_max(const T (&c)[C::R], const Sh2<C>& sh, con
 
 // The base periods scored by one launch: records [t0[i], t0[i + 1]) belong
 // to entry i, whose profiles have p0[i] bins and whose plane starts at
-// element off[i] of `prof` (all share m_rows and the widths).  A single base
-// period is a group of one.
+// element off[i] of `prof` with rows ld[i] elements apart (all share m_rows
+// and the widths); record it of entry i goes to rec[i][it - t0[i]].  A
+// single base period is a group of one.  Entries may come from different
+// series (a batch): each has its own records.
 struct ScoreGroup {
     int32_t n;
     int64_t t0[FOLD_GROUP_MAX + 1];
     int32_t p0[FOLD_GROUP_MAX];
     int64_t off[FOLD_GROUP_MAX];
+    int64_t ld[FOLD_GROUP_MAX];
+    ffa_record* rec[FOLD_GROUP_MAX];
 };
 
 __device__ __forceinline__ int score_entry(const ScoreGroup& g, int64_t it) {
@@ -574,8 +578,7 @@ __device__ __forceinline__ int score_entry(const ScoreGroup& g, int64_t it) {
 template <class C, class T, bool FUSED>
 __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ prof_all, const ScoreGroup sg,
                                                           int64_t m_rows, int64_t trial0, int64_t count,
-                                                          ScoreWidths wd, ffa_record* __restrict__ rec,
-                                                          int32_t* d_status) {
+                                                          ScoreWidths wd, int32_t* d_status) {
     FFA_CFG_ALIASES
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sh2<C>& sh = *reinterpret_cast<Sh2<C>*>(smem_raw);
@@ -597,11 +600,11 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         if (it + gridDim.x < count) {
             const int64_t itn = it + gridDim.x;
             const int en = score_entry(sg, itn);
-            const int64_t pn = sg.p0[en];
+            const int64_t pn = sg.p0[en], ln = sg.ld[en];
             const T* prn = prof_all + sg.off[en];
             const int64_t kn = trial0 + (itn - sg.t0[en]);
-            const T* nh = FUSED ? (m_rows > 1 ? prn + (kn >> 1) * pn : prn) : prn + kn * pn;
-            const T* nt = (FUSED && m_rows > 1) ? prn + ((m_rows >> 1) + (kn >> 1)) * pn : nullptr;
+            const T* nh = FUSED ? (m_rows > 1 ? prn + (kn >> 1) * ln : prn) : prn + kn * ln;
+            const T* nt = (FUSED && m_rows > 1) ? prn + ((m_rows >> 1) + (kn >> 1)) * ln : nullptr;
             const int lines = (int)((pn * (int64_t)sizeof(T) + 127) / 128);
             for (int l = tid; l < lines; l += T2) {
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(nh + l * (128 / sizeof(T))));
@@ -615,14 +618,15 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     const T* hrow;
     const T* trow = nullptr;
     int sft = 0;
+    const int64_t ld_ = sg.ld[ei];
     if (FUSED && m_rows > 1) {
-        hrow = prof + (k >> 1) * p0_;
-        trow = prof + ((m_rows >> 1) + (k >> 1)) * p0_;
+        hrow = prof + (k >> 1) * ld_;
+        trow = prof + ((m_rows >> 1) + (k >> 1)) * ld_;
         sft = (int)((uint32_t)((k + 1) >> 1) % (uint32_t)p0);
     } else if (FUSED) {
         hrow = prof;
     } else {
-        hrow = prof + k * p0_;
+        hrow = prof + k * ld_;
     }
     // the sum, sum of squares and largest |x| (they only scale the median's
     // buckets) accumulate as the profile is loaded
@@ -1310,7 +1314,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
             out.flags = 0;
             if (pos == 0x7fffffff) dev_fail(d_status, FFA_ERR_DEVICE);
         }
-        rec[it] = out;
+        sg.rec[ei][it - sg.t0[ei]] = out;
     }
     __syncthreads();
     }  // trials
@@ -1340,8 +1344,7 @@ __device__ __forceinline__ T box_at(const T (&c)[C::R], const Sh2<C>& sh, const 
 template <class C, class T, bool FUSED>
 __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restrict__ prof_all, const ScoreGroup sg,
                                                               int64_t m_rows, int64_t trial0, int64_t count,
-                                                              ScoreWidths wd, float excl_frac,
-                                                              ffa_record* __restrict__ rec) {
+                                                              ScoreWidths wd, float excl_frac) {
     FFA_CFG_ALIASES
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sh2<C>& sh = *reinterpret_cast<Sh2<C>*>(smem_raw);
@@ -1362,14 +1365,15 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
         const T* hrow;
         const T* trow = nullptr;
         int sft = 0;
+        const int64_t ld_ = sg.ld[ei];
         if (FUSED && m_rows > 1) {
-            hrow = prof + (k >> 1) * p0_;
-            trow = prof + ((m_rows >> 1) + (k >> 1)) * p0_;
+            hrow = prof + (k >> 1) * ld_;
+            trow = prof + ((m_rows >> 1) + (k >> 1)) * ld_;
             sft = (int)(((k + 1) >> 1) % p0_);
         } else if (FUSED) {
             hrow = prof;
         } else {
-            hrow = prof + k * p0_;
+            hrow = prof + k * ld_;
         }
         if (trow) {
             const int n1 = p0 - sft;
@@ -1565,7 +1569,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
                 out.phase = best_j;
                 out.flags = 0;
             }
-            rec[it] = out;
+            sg.rec[ei][it - sg.t0[ei]] = out;
         }
         __syncthreads();
     }
@@ -1626,8 +1630,8 @@ ffa_status launch_score2_cfg(const void* d_prof, const ScoreGroup& sg, int64_t c
     es = resident_ctas(fn, C::T, smem, &resident);
     if (es != FFA_OK) return es;
     const unsigned grid = (unsigned)(count < resident ? count : resident);
-    k_score2<C, TT, FF><<<grid, C::T, smem, st>>>((const TT*)d_prof, sg, m_rows, trial0, count, wd, d_rec,
-                                                  d_status);
+    (void)d_rec;  // the records go where sg.rec points
+    k_score2<C, TT, FF><<<grid, C::T, smem, st>>>((const TT*)d_prof, sg, m_rows, trial0, count, wd, d_status);
     FFA_LAUNCH_CHECK("k_score2");
     count_launch();
     return FFA_OK;
@@ -1649,13 +1653,29 @@ ffa_status launch_score2_t(const void* d_prof, const ScoreGroup& sg, int64_t cou
     return launch_score2_cfg<CBig, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
 }
 
-ScoreGroup single(int64_t p0, int64_t count) {
+}  // namespace
+
+// The scorer's CTA shape for a profile of p0 bins (0: 256 x 8, 1: 512 x 16,
+// 2: 1024 x 16, 3: 1024 x 32); grouped launches hold one shape only, so a
+// profile's record does not depend on what it is grouped with.
+int score_shape(int64_t p0, int wmax) {
+    if (fits<Cfg<256>>(p0, wmax)) return 0;
+    if (fits<Cfg<512>>(p0, wmax)) return 1;
+    if (fits<CMid>(p0, wmax)) return 2;
+    return 3;
+}
+
+namespace {
+
+ScoreGroup single(int64_t p0, int64_t ld, int64_t count, ffa_record* d_rec) {
     ScoreGroup sg;
     sg.n = 1;
     sg.t0[0] = 0;
     sg.t0[1] = count;
     sg.p0[0] = (int32_t)p0;
     sg.off[0] = 0;
+    sg.ld[0] = ld;
+    sg.rec[0] = d_rec;
     return sg;
 }
 
@@ -1675,14 +1695,14 @@ ffa_status score2_dispatch(const void* d_prof, const ScoreGroup& sg, int32_t pre
 }  // namespace
 
 ffa_status launch_score2(const void* d_prof, int32_t precision, bool fused, int64_t count,
-                         int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
+                         int64_t trial0, int64_t p0, int64_t ld, int64_t m_rows, const ScoreWidths& wd,
                          ffa_record* d_rec, int32_t* d_status, cudaStream_t st) {
-    return score2_dispatch(d_prof, single(p0, count), precision, fused, count, trial0, p0, m_rows, wd, d_rec,
+    return score2_dispatch(d_prof, single(p0, ld, count, d_rec), precision, fused, count, trial0, p0, m_rows, wd, d_rec,
                            d_status, st);
 }
 
 ffa_status launch_score2_group(const void* d_plane, int32_t precision, int n, const int64_t* p0, const int64_t* off,
-                               int64_t m_rows, const ScoreWidths& wd, ffa_record* d_rec, int32_t* d_status,
+                               int64_t m_rows, const ScoreWidths& wd, ffa_record* const* recs, int32_t* d_status,
                                cudaStream_t st) {
     if (n < 1 || n > FOLD_GROUP_MAX) return fail(FFA_ERR_ARG, "score group: 1..FOLD_GROUP_MAX base periods");
     ScoreGroup sg;
@@ -1692,11 +1712,13 @@ ffa_status launch_score2_group(const void* d_plane, int32_t precision, int n, co
         sg.t0[i] = (int64_t)i * m_rows;
         sg.p0[i] = (int32_t)p0[i];
         sg.off[i] = off[i];
+        sg.ld[i] = plane_pitch(p0[i]);
+        sg.rec[i] = recs[i];
         p0max = p0[i] > p0max ? p0[i] : p0max;
     }
     sg.t0[n] = (int64_t)n * m_rows;
-    return score2_dispatch(d_plane, sg, precision, true, (int64_t)n * m_rows, 0, p0max, m_rows, wd, d_rec, d_status,
-                           st);
+    return score2_dispatch(d_plane, sg, precision, true, (int64_t)n * m_rows, 0, p0max, m_rows, wd, recs[0],
+                           d_status, st);
 }
 
 namespace {
@@ -1715,8 +1737,9 @@ ffa_status launch_alg2_cfg(const void* d_prof, const ScoreGroup& sg, int64_t cou
     es = resident_ctas(fn, C::T, smem, &resident);
     if (es != FFA_OK) return es;
     const unsigned grid = (unsigned)(count < resident ? count : resident);
+    (void)d_rec;  // the records go where sg.rec points
     k_score_alg2<C, TT, FF><<<grid, C::T, smem, st>>>((const TT*)d_prof, sg, m_rows, trial0, count, wd,
-                                                      excl_frac, d_rec);
+                                                      excl_frac);
     FFA_LAUNCH_CHECK("k_score_alg2");
     count_launch();
     return FFA_OK;
@@ -1752,15 +1775,15 @@ ffa_status alg2_dispatch(const void* d_prof, const ScoreGroup& sg, int32_t preci
 }  // namespace
 
 ffa_status launch_score_alg2(const void* d_prof, int32_t precision, bool fused, int64_t count,
-                             int64_t trial0, int64_t p0, int64_t m_rows, const ScoreWidths& wd,
+                             int64_t trial0, int64_t p0, int64_t ld, int64_t m_rows, const ScoreWidths& wd,
                              float excl_frac, ffa_record* d_rec, cudaStream_t st) {
-    return alg2_dispatch(d_prof, single(p0, count), precision, fused, count, trial0, p0, m_rows, wd, excl_frac,
+    return alg2_dispatch(d_prof, single(p0, ld, count, d_rec), precision, fused, count, trial0, p0, m_rows, wd, excl_frac,
                          d_rec, st);
 }
 
 ffa_status launch_score_alg2_group(const void* d_plane, int32_t precision, int n, const int64_t* p0,
                                    const int64_t* off, int64_t m_rows, const ScoreWidths& wd, float excl_frac,
-                                   ffa_record* d_rec, cudaStream_t st) {
+                                   ffa_record* const* recs, cudaStream_t st) {
     if (n < 1 || n > FOLD_GROUP_MAX) return fail(FFA_ERR_ARG, "score group: 1..FOLD_GROUP_MAX base periods");
     ScoreGroup sg;
     sg.n = n;
@@ -1769,11 +1792,13 @@ ffa_status launch_score_alg2_group(const void* d_plane, int32_t precision, int n
         sg.t0[i] = (int64_t)i * m_rows;
         sg.p0[i] = (int32_t)p0[i];
         sg.off[i] = off[i];
+        sg.ld[i] = plane_pitch(p0[i]);
+        sg.rec[i] = recs[i];
         p0max = p0[i] > p0max ? p0[i] : p0max;
     }
     sg.t0[n] = (int64_t)n * m_rows;
     return alg2_dispatch(d_plane, sg, precision, true, (int64_t)n * m_rows, 0, p0max, m_rows, wd, excl_frac,
-                         d_rec, st);
+                         recs[0], st);
 }
 
 }  // namespace ffa

@@ -39,6 +39,20 @@ ffa_status cuda_fail(cudaError_t e, const char* where) {
 static std::atomic<long long> g_launches{0};
 void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+int sm_count() {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    cache[dev] = n;
+    return n;
+}
+
 ffa_status ensure_smem(const void* func, size_t bytes) {
     static std::mutex mu;
     static std::map<std::pair<const void*, int>, size_t> done;
@@ -266,7 +280,9 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr int64_t GROUP_TRIALS = 1024;
 constexpr int64_t GROUP_ELEMS = (int64_t)1 << 24;
 // elements a base period's plane takes in a group (256-byte aligned)
-static size_t plane_slot(const ffa_plan_entry& e) { return ((size_t)e.m_rows * e.p0 + 63) & ~(size_t)63; }
+static size_t plane_slot(const ffa_plan_entry& e) {
+    return ((size_t)e.m_rows * (size_t)plane_pitch(e.p0) + 63) & ~(size_t)63;
+}
 
 extern "C" {
 
@@ -377,7 +393,7 @@ ffa_status ffa_plan_create(const ffa_search_config* cfg, int64_t n, ffa_plan** o
             }
             p->entries.push_back(e);
             p->n_trials += m;
-            p->max_plane = std::max<int64_t>(p->max_plane, m * p0);
+            p->max_plane = std::max<int64_t>(p->max_plane, m * plane_pitch(p0));
         }
         int64_t cnt = (int64_t)p->entries.size() - first;
         if (cnt > 0) {
@@ -449,6 +465,29 @@ ffa_status ffa_plan_entries(const ffa_plan* p, ffa_plan_entry* out, int64_t cap)
     return FFA_OK;
 }
 
+ffa_status ffa_plan_periods(const ffa_plan* p, int64_t trial_begin, int64_t count, double* out) {
+    if (!p) return fail(FFA_ERR_ARG, "plan_periods: null plan");
+    if (count < 0 || trial_begin < 0 || trial_begin > p->n_trials || count > p->n_trials - trial_begin)
+        return fail(FFA_ERR_ARG, "plan_periods: trial range outside the periodogram");
+    if (count > 0 && !out) return fail(FFA_ERR_ARG, "plan_periods: null output");
+    if (count == 0) return FFA_OK;
+    // the entry holding trial_begin, then consecutive trials entry by entry
+    size_t e = (size_t)(std::upper_bound(p->entries.begin(), p->entries.end(), trial_begin,
+                                         [](int64_t t, const ffa_plan_entry& x) { return t < x.first_trial; }) -
+                        p->entries.begin()) - 1;
+    const double ts = p->cfg.tsamp_s * (double)p->cfg.downsample0;
+    for (int64_t i = 0; i < count; ++i) {
+        const int64_t t = trial_begin + i;
+        while (t >= p->entries[e].first_trial + p->entries[e].m_rows) ++e;
+        const ffa_plan_entry& en = p->entries[e];
+        const int64_t k = t - en.first_trial;
+        // Eq. 2 with the padded N = M * P0: P0 + k P0 / (N - P0) = P0 + k / (M - 1) samples
+        const double frac = en.m_rows > 1 ? (double)k / (double)(en.m_rows - 1) : 0.0;
+        out[i] = ((double)en.p0 + frac) * ts * std::ldexp(1.0, en.octave);
+    }
+    return FFA_OK;
+}
+
 // The pipeline for plan entries [e0, e1): every octave holding one of them is
 // prepared (downsampled, dereddened, normalised); only those base periods are
 // folded and scored.
@@ -470,7 +509,8 @@ static int64_t group_end(const ffa_plan* p, int64_t t, int64_t b) {
     while (j < b && j - t < FOLD_GROUP_MAX) {
         const ffa_plan_entry& e = p->entries[(size_t)j];
         if (e.octave != e0.octave || e.m_rows != e0.m_rows || lg(e.p0) != lg(e0.p0) || e.n_widths != e0.n_widths ||
-            std::memcmp(e.widths, e0.widths, sizeof(int32_t) * (size_t)e0.n_widths) != 0)
+            std::memcmp(e.widths, e0.widths, sizeof(int32_t) * (size_t)e0.n_widths) != 0 ||
+            score_shape(e.p0, e.widths[e.n_widths - 1]) != score_shape(e0.p0, e0.widths[e0.n_widths - 1]))
             break;
         if (elems + plane_slot(e) > (size_t)p->plane_elems || trials + e.m_rows > GROUP_TRIALS) break;
         elems += plane_slot(e);
@@ -478,6 +518,37 @@ static int64_t group_end(const ffa_plan* p, int64_t t, int64_t b) {
         ++j;
     }
     return j > t ? j : t + 1;
+}
+
+// Prepare octave `oct` of the series in the workspace: the D0 sums, the
+// octave downsampling chain on the raw series, the dereddening (resid) and the
+// normalised fold input (z).  The debug outputs below use it.
+static ffa_status prepare_octave(const ffa_plan* p, const void* d_series, char* ws, int32_t oct,
+                                 int32_t* d_status, cudaStream_t st, int64_t* n_out) {
+    const ffa_search_config& c = p->cfg;
+    double* raw[2] = {(double*)(ws + p->off_raw_a), (double*)(ws + p->off_raw_b)};
+    double* resid = (double*)(ws + p->off_resid);
+    ffa_status s = launch_downsample(d_series, c.in_type, p->n, c.downsample0, raw[0], st);
+    if (s != FFA_OK) return s;
+    int64_t n_o = p->n0;
+    for (int32_t o = 1; o <= oct; ++o) {
+        s = launch_downsample(raw[(o - 1) & 1], FFA_IN_F64, n_o, 2, raw[o & 1], st);
+        if (s != FFA_OK) return s;
+        n_o /= 2;
+    }
+    double* cur = raw[oct & 1];
+    if (p->window > 1) {
+        s = launch_detrend(cur, n_o, p->window, resid, d_status, st);
+    } else {
+        cudaError_t e = cudaMemcpyAsync(resid, cur, sizeof(double) * n_o, cudaMemcpyDeviceToDevice, st);
+        count_launch();
+        s = e == cudaSuccess ? FFA_OK : cuda_fail(e, "prepare: copy");
+    }
+    if (s != FFA_OK) return s;
+    s = launch_normalise(resid, n_o, c.precision, ws + p->off_z, (double*)(ws + p->off_stats), st,
+                         c.clip_sigma, c.persist_cutoff, nullptr);
+    *n_out = n_o;
+    return s;
 }
 
 static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_ws, size_t ws_bytes,
@@ -549,23 +620,30 @@ static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_
                     offs[i] = off;
                     off += (int64_t)plane_slot(ei);
                 }
+                // per-kernel timing of the groups holding an every-TIMING_SAMPLE-th base period
+                const int64_t r0 = t - p->oct_first[o], r1 = t1 - 1 - p->oct_first[o];
+                const bool gsample = (r0 % TIMING_SAMPLE) == 0 || r0 / TIMING_SAMPLE != r1 / TIMING_SAMPLE;
+                PhaseTimer gfold_k(4, o, st, gsample);
                 s = launch_fold_group(z, c.precision, n, p0s, mds, offs, e.m_rows, m > 0 ? m - 1 : 0, plane0,
                                       plane1, st);
                 if (s != FFA_OK) return s;
+                gfold_k.stop();
+                PhaseTimer gscore_k(5, o, st, gsample);
+                ffa_record* recs[FOLD_GROUP_MAX];
+                for (int i = 0; i < n; ++i) recs[i] = d_records + p->entries[(size_t)(t + i)].first_trial;
                 if (c.scorer == FFA_SCORE_ALG2)
-                    s = launch_score_alg2_group(plane0, c.precision, n, p0s, offs, e.m_rows, wd, excl,
-                                                d_records + e.first_trial, st);
+                    s = launch_score_alg2_group(plane0, c.precision, n, p0s, offs, e.m_rows, wd, excl, recs, st);
                 else
-                    s = launch_score2_group(plane0, c.precision, n, p0s, offs, e.m_rows, wd,
-                                            d_records + e.first_trial, d_status, st);
+                    s = launch_score2_group(plane0, c.precision, n, p0s, offs, e.m_rows, wd, recs, d_status, st);
                 if (s != FFA_OK) return s;
+                gscore_k.stop();
                 if (d_persist) {
                     s = launch_fold_group(bits, FFA_FOLD_I8, n, p0s, mds, offs, e.m_rows, m > 0 ? m - 1 : 0, plane0,
                                           plane1, st);
                     if (s != FFA_OK) return s;
                     for (int i = 0; i < n; ++i) {
                         const ffa_plan_entry& ei = p->entries[(size_t)(t + i)];
-                        s = launch_persist((const int32_t*)plane0 + offs[i], ei.m_rows, ei.p0,
+                        s = launch_persist((const int32_t*)plane0 + offs[i], ei.m_rows, ei.p0, plane_pitch(ei.p0),
                                            d_records + ei.first_trial, d_persist + ei.first_trial, st);
                         if (s != FFA_OK) return s;
                     }
@@ -577,25 +655,26 @@ static ffa_status search_range(const ffa_plan* p, const void* d_series, void* d_
             const bool sample = ((t - p->oct_first[o]) % TIMING_SAMPLE) == 0;
             // all but the last stage; the scorer applies the last one while loading
             PhaseTimer fold_k(2, o, st, sample);
-            s = launch_fold(z, c.precision, e.p0, e.m_data, e.m_rows, m > 0 ? m - 1 : 0, plane0,
+            const int64_t ld = plane_pitch(e.p0);
+            s = launch_fold(z, c.precision, e.p0, e.m_data, e.m_rows, m > 0 ? m - 1 : 0, ld, plane0,
                             plane1, st);
             if (s != FFA_OK) return s;
             fold_k.stop();
             PhaseTimer score_k(3, o, st, sample);
             if (c.scorer == FFA_SCORE_ALG2)
-                s = launch_score_alg2(plane0, c.precision, true, e.m_rows, 0, e.p0, e.m_rows, wd, excl,
+                s = launch_score_alg2(plane0, c.precision, true, e.m_rows, 0, e.p0, ld, e.m_rows, wd, excl,
                                       d_records + e.first_trial, st);
             else
-                s = launch_score2(plane0, c.precision, true, e.m_rows, 0, e.p0, e.m_rows, wd,
+                s = launch_score2(plane0, c.precision, true, e.m_rows, 0, e.p0, ld, e.m_rows, wd,
                                   d_records + e.first_trial, d_status, st);
             if (s != FFA_OK) return s;
             score_k.stop();
             if (d_persist) {
                 // the 0/1 series through the same fold, then each trial's window sum
-                s = launch_fold(bits, FFA_FOLD_I8, e.p0, e.m_data, e.m_rows, m > 0 ? m - 1 : 0,
+                s = launch_fold(bits, FFA_FOLD_I8, e.p0, e.m_data, e.m_rows, m > 0 ? m - 1 : 0, ld,
                                 plane0, plane1, st);
                 if (s != FFA_OK) return s;
-                s = launch_persist((const int32_t*)plane0, e.m_rows, e.p0, d_records + e.first_trial,
+                s = launch_persist((const int32_t*)plane0, e.m_rows, e.p0, ld, d_records + e.first_trial,
                                    d_persist + e.first_trial, st);
                 if (s != FFA_OK) return s;
             }
@@ -626,7 +705,8 @@ ffa_status ffa_autotune(const ffa_plan* p, void* d_ws, size_t ws_bytes, void* st
     for (auto& g : groups) {
         const ffa_plan_entry& e = p->entries[g.second[g.second.size() / 2]];  // the median base period
         ffa_status s = tune_fold(ws + p->off_z, p->cfg.precision, e.p0, e.m_data, e.m_rows, g.first.first,
-                                 ws + p->off_plane0, ws + p->off_plane1, as_stream(stream), nullptr);
+                                 plane_pitch(e.p0), ws + p->off_plane0, ws + p->off_plane1, as_stream(stream),
+                                 nullptr);
         if (s != FFA_OK) return s;
         ++n;
     }
@@ -658,18 +738,265 @@ ffa_status ffa_search_entries(const ffa_plan* p, const void* d_series, int64_t e
                         entry_begin, entry_end);
 }
 
+ffa_status ffa_search_series(const ffa_plan* p, const void* d_series, int32_t octave, int32_t what,
+                             void* d_ws, size_t ws_bytes, void* d_out, int32_t* d_status, void* stream) {
+    if (!p) return fail(FFA_ERR_ARG, "search_series: null plan");
+    if (octave < 0 || octave >= p->n_octaves) return fail(FFA_ERR_ARG, "search_series: octave outside the plan");
+    if (what != FFA_DUMP_RESID && what != FFA_DUMP_Z) return fail(FFA_ERR_ARG, "search_series: bad `what`");
+    if (!d_series || !d_ws || !d_out) return fail(FFA_ERR_ARG, "search_series: null buffer");
+    if (ws_bytes < p->ws_bytes) return fail(FFA_ERR_OOM, "search_series: workspace too small");
+    if ((uintptr_t)d_ws % 256 != 0) return fail(FFA_ERR_ARG, "search_series: workspace not 256-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    char* ws = (char*)d_ws;
+    int64_t n_o = 0;
+    ffa_status s = prepare_octave(p, d_series, ws, octave, d_status, st, &n_o);
+    if (s != FFA_OK) return s;
+    const void* src = what == FFA_DUMP_RESID ? (const void*)(ws + p->off_resid) : (const void*)(ws + p->off_z);
+    const size_t esz = what == FFA_DUMP_RESID ? 8 : (p->cfg.precision == FFA_FOLD_F32 ? 4 : 1);
+    cudaError_t e = cudaMemcpyAsync(d_out, src, esz * (size_t)n_o, cudaMemcpyDeviceToDevice, st);
+    count_launch();
+    return e == cudaSuccess ? FFA_OK : cuda_fail(e, "search_series: copy");
+}
+
+ffa_status ffa_search_plane(const ffa_plan* p, const void* d_series, int64_t entry, void* d_ws, size_t ws_bytes,
+                            void* d_plane, int32_t* d_status, void* stream) {
+    if (!p) return fail(FFA_ERR_ARG, "search_plane: null plan");
+    if (entry < 0 || entry >= (int64_t)p->entries.size()) return fail(FFA_ERR_ARG, "search_plane: entry outside the plan");
+    if (!d_series || !d_ws || !d_plane) return fail(FFA_ERR_ARG, "search_plane: null buffer");
+    if (ws_bytes < p->ws_bytes) return fail(FFA_ERR_OOM, "search_plane: workspace too small");
+    if ((uintptr_t)d_ws % 256 != 0) return fail(FFA_ERR_ARG, "search_plane: workspace not 256-byte aligned");
+    cudaStream_t st = as_stream(stream);
+    char* ws = (char*)d_ws;
+    const ffa_plan_entry& e = p->entries[(size_t)entry];
+    int64_t n_o = 0;
+    ffa_status s = prepare_octave(p, d_series, ws, e.octave, d_status, st, &n_o);
+    if (s != FFA_OK) return s;
+    // every stage on the search's padded-pitch planes, then the rows packed
+    // densely into the caller's plane
+    const int64_t ld = plane_pitch(e.p0);
+    s = launch_fold(ws + p->off_z, p->cfg.precision, e.p0, e.m_data, e.m_rows, -1, ld, ws + p->off_plane0,
+                    ws + p->off_plane1, st);
+    if (s != FFA_OK) return s;
+    const size_t esz = 4;  // float or int32
+    cudaError_t ce = cudaMemcpy2DAsync(d_plane, esz * (size_t)e.p0, ws + p->off_plane0, esz * (size_t)ld,
+                                       esz * (size_t)e.p0, (size_t)e.m_rows, cudaMemcpyDeviceToDevice, st);
+    count_launch();
+    return ce == cudaSuccess ? FFA_OK : cuda_fail(ce, "search_plane: copy");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched search: many series (e.g. dedispersion trials of uneven length)
+// with one configuration.  Octave by octave, every series is prepared into
+// its own slice of the workspace, then the base periods of all series are
+// folded and scored together: items with the same rows, widths, scorer
+// shape and floor(log2 P0) -- from any series -- share one set of fold
+// launches and one persistent scorer launch (up to FOLD_GROUP_MAX base
+// periods and BATCH_GROUP_ELEMS plane elements per group), each reading its
+// own series and writing its own series' records.  Every base period runs
+// the same kernels with the same add tree and scorer shape as in ffa_search,
+// so the records are those of each series searched alone.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t BATCH_GROUP_ELEMS = (int64_t)1 << 25;  // per plane buffer (32-bit elements)
+
+struct BatchLayout {
+    std::vector<size_t> raw_off, z_off;
+    size_t off_tmp = 0, off_resid = 0, off_stats = 0, off_plane0 = 0, off_plane1 = 0, bytes = 0;
+    int64_t plane_elems = 0;
+};
+
+ffa_status batch_layout(const ffa_plan* const* plans, int32_t count, BatchLayout* L) {
+    if (count < 1 || !plans) return fail(FFA_ERR_ARG, "batch: need at least one plan");
+    for (int32_t i = 0; i < count; ++i) {
+        if (!plans[i]) return fail(FFA_ERR_ARG, "batch: null plan");
+        if (std::memcmp(&plans[i]->cfg, &plans[0]->cfg, sizeof(ffa_search_config)) != 0)
+            return fail(FFA_ERR_ARG, "batch: every plan needs the same configuration (lengths may differ)");
+    }
+    if (plans[0]->cfg.persistence) return fail(FFA_ERR_UNSUPPORTED, "batch: persistence plans are searched one by one");
+    const size_t esz = plans[0]->cfg.precision == FFA_FOLD_F32 ? 4 : 1;
+    int64_t max_n0 = 1, max_slot = 1;
+    size_t off = 0;
+    L->raw_off.resize((size_t)count);
+    L->z_off.resize((size_t)count);
+    for (int32_t i = 0; i < count; ++i) {
+        const int64_t n0 = std::max<int64_t>(plans[i]->n0, 1);
+        max_n0 = std::max(max_n0, n0);
+        for (const ffa_plan_entry& e : plans[i]->entries) max_slot = std::max<int64_t>(max_slot, (int64_t)plane_slot(e));
+        L->raw_off[(size_t)i] = off;
+        off = align256(off + sizeof(double) * (size_t)n0);
+    }
+    for (int32_t i = 0; i < count; ++i) {
+        L->z_off[(size_t)i] = off;
+        off = align256(off + esz * (size_t)std::max<int64_t>(plans[i]->n0, 1));
+    }
+    L->off_tmp = off;
+    off = align256(off + sizeof(double) * (size_t)(max_n0 / 2 + 1));
+    L->off_resid = off;
+    off = align256(off + sizeof(double) * (size_t)max_n0);
+    L->off_stats = off;
+    off = align256(off + sizeof(double) * STATS_DOUBLES);
+    L->plane_elems = std::max<int64_t>(max_slot, std::min<int64_t>(BATCH_GROUP_ELEMS, (int64_t)count * max_slot));
+    L->off_plane0 = off;
+    off = align256(off + 4 * (size_t)L->plane_elems);
+    L->off_plane1 = off;
+    off = align256(off + 4 * (size_t)L->plane_elems);
+    L->bytes = off;
+    return FFA_OK;
+}
+
+struct BatchItem {
+    int32_t series;
+    const ffa_plan_entry* e;
+    int shape, lg;
+};
+
+int lg2(int64_t v) {
+    int r = 0;
+    while ((int64_t)2 << r <= v) ++r;
+    return r;
+}
+
+bool batch_compatible(const BatchItem& a, const BatchItem& b) {
+    return a.e->m_rows == b.e->m_rows && a.shape == b.shape && a.lg == b.lg && a.e->n_widths == b.e->n_widths &&
+           std::memcmp(a.e->widths, b.e->widths, sizeof(int32_t) * (size_t)a.e->n_widths) == 0;
+}
+}  // namespace
+
+extern "C" {
+
+ffa_status ffa_batch_workspace_bytes(const ffa_plan* const* plans, int32_t count, size_t* bytes) {
+    if (!bytes) return fail(FFA_ERR_ARG, "batch_workspace_bytes: null output");
+    BatchLayout L;
+    ffa_status s = batch_layout(plans, count, &L);
+    if (s != FFA_OK) return s;
+    *bytes = L.bytes;
+    return FFA_OK;
+}
+
 ffa_status ffa_search_batch(const ffa_plan* const* plans, const void* const* d_series, int32_t count,
                             void* d_ws, size_t ws_bytes, ffa_record* const* d_records,
                             int32_t* d_status, void* stream) {
-    if (count < 0 || (count > 0 && (!plans || !d_series || !d_records)))
-        return fail(FFA_ERR_ARG, "search_batch: null argument");
+    if (count < 0) return fail(FFA_ERR_ARG, "search_batch: negative count");
+    if (count == 0) return FFA_OK;
+    if (!d_series || !d_records) return fail(FFA_ERR_ARG, "search_batch: null argument");
+    BatchLayout L;
+    ffa_status s = batch_layout(plans, count, &L);
+    if (s != FFA_OK) return s;
+    if (!d_ws) return fail(FFA_ERR_ARG, "search_batch: null workspace");
+    if (ws_bytes < L.bytes) return fail(FFA_ERR_OOM, "search_batch: workspace too small (ffa_batch_workspace_bytes)");
+    if ((uintptr_t)d_ws % 256 != 0) return fail(FFA_ERR_ARG, "search_batch: workspace not 256-byte aligned");
+    for (int32_t i = 0; i < count; ++i)
+        if (plans[i]->n_trials > 0 && (!d_series[i] || !d_records[i]))
+            return fail(FFA_ERR_ARG, "search_batch: null series or records");
+    const ffa_search_config& c = plans[0]->cfg;
+    const int32_t window = plans[0]->window;
+    cudaStream_t st = as_stream(stream);
+    char* ws = (char*)d_ws;
+    double* tmp = (double*)(ws + L.off_tmp);
+    double* resid = (double*)(ws + L.off_resid);
+    double* stats = (double*)(ws + L.off_stats);
+    void* plane0 = ws + L.off_plane0;
+    void* plane1 = ws + L.off_plane1;
+    const size_t esz = c.precision == FFA_FOLD_F32 ? 4 : 1;
+    int32_t max_oct = 0;
+    std::vector<int64_t> n_o((size_t)count);
     for (int32_t i = 0; i < count; ++i) {
-        if (!plans[i]) return fail(FFA_ERR_ARG, "search_batch: null plan");
-        if (ws_bytes < plans[i]->ws_bytes) return fail(FFA_ERR_OOM, "search_batch: workspace too small");
+        max_oct = std::max(max_oct, plans[i]->n_octaves);
+        n_o[(size_t)i] = plans[i]->n0;
+        if (plans[i]->n_octaves > 0) {
+            s = launch_downsample(d_series[i], c.in_type, plans[i]->n, c.downsample0, (double*)(ws + L.raw_off[(size_t)i]),
+                                  st);
+            if (s != FFA_OK) return s;
+        }
     }
-    for (int32_t i = 0; i < count; ++i) {
-        ffa_status s = ffa_search(plans[i], d_series[i], d_ws, ws_bytes, d_records[i], d_status, stream);
-        if (s != FFA_OK) return s;
+    const float excl = c.alg2_window > 0.0f ? c.alg2_window : 0.2f;
+    for (int32_t o = 0; o < max_oct; ++o) {
+        PhaseTimer prep_t(0, o, st);
+        std::vector<BatchItem> items;
+        for (int32_t i = 0; i < count; ++i) {
+            const ffa_plan* p = plans[i];
+            if (p->n_octaves <= o) continue;
+            double* raw = (double*)(ws + L.raw_off[(size_t)i]);
+            int64_t& n = n_o[(size_t)i];
+            if (o > 0) {
+                s = launch_downsample(raw, FFA_IN_F64, n, 2, tmp, st);
+                if (s != FFA_OK) return s;
+                n /= 2;
+                cudaError_t ce = cudaMemcpyAsync(raw, tmp, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+                count_launch();
+                if (ce != cudaSuccess) return cuda_fail(ce, "search_batch: copy");
+            }
+            if (window > 1) {
+                s = launch_detrend(raw, n, window, resid, d_status, st);
+            } else {
+                cudaError_t ce = cudaMemcpyAsync(resid, raw, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+                count_launch();
+                s = ce == cudaSuccess ? FFA_OK : cuda_fail(ce, "search_batch: copy");
+            }
+            if (s != FFA_OK) return s;
+            s = launch_normalise(resid, n, c.precision, ws + L.z_off[(size_t)i], stats, st, c.clip_sigma, c.persist_cutoff,
+                                 nullptr);
+            if (s != FFA_OK) return s;
+            const int64_t a = p->oct_first[(size_t)o], b = a + p->oct_count[(size_t)o];
+            for (int64_t t = a; t < b; ++t) {
+                const ffa_plan_entry& e = p->entries[(size_t)t];
+                items.push_back(BatchItem{i, &e, score_shape(e.p0, e.widths[e.n_widths - 1]), lg2(e.p0)});
+            }
+        }
+        prep_t.stop();
+        PhaseTimer fold_t(1, o, st);
+        std::stable_sort(items.begin(), items.end(), [](const BatchItem& x, const BatchItem& y) {
+            if (x.e->m_rows != y.e->m_rows) return x.e->m_rows > y.e->m_rows;
+            if (x.shape != y.shape) return x.shape < y.shape;
+            if (x.lg != y.lg) return x.lg < y.lg;
+            if (x.e->n_widths != y.e->n_widths) return x.e->n_widths < y.e->n_widths;
+            const int wc = std::memcmp(x.e->widths, y.e->widths, sizeof(int32_t) * (size_t)x.e->n_widths);
+            if (wc != 0) return wc < 0;
+            return x.e->p0 < y.e->p0;
+        });
+        for (size_t t = 0; t < items.size();) {
+            size_t j = t;
+            int64_t elems = 0;
+            while (j < items.size() && j - t < (size_t)FOLD_GROUP_MAX && batch_compatible(items[j], items[t]) &&
+                   elems + (int64_t)plane_slot(*items[j].e) <= L.plane_elems) {
+                elems += (int64_t)plane_slot(*items[j].e);
+                ++j;
+            }
+            if (j == t) ++j;
+            const int n = (int)(j - t);
+            const ffa_plan_entry& e0 = *items[t].e;
+            int m = 0;
+            while ((1 << m) < e0.m_rows) ++m;
+            int64_t p0s[FOLD_GROUP_MAX], mds[FOLD_GROUP_MAX], offs[FOLD_GROUP_MAX];
+            const void* srcs[FOLD_GROUP_MAX];
+            ffa_record* recs[FOLD_GROUP_MAX];
+            int64_t off = 0;
+            for (int k = 0; k < n; ++k) {
+                const BatchItem& it = items[t + (size_t)k];
+                p0s[k] = it.e->p0;
+                mds[k] = it.e->m_data;
+                offs[k] = off;
+                off += (int64_t)plane_slot(*it.e);
+                srcs[k] = ws + L.z_off[(size_t)it.series];
+                recs[k] = d_records[it.series] + it.e->first_trial;
+            }
+            (void)esz;
+            s = launch_fold_group(srcs[0], c.precision, n, p0s, mds, offs, e0.m_rows, m > 0 ? m - 1 : 0, plane0, plane1,
+                                  st, srcs);
+            if (s != FFA_OK) return s;
+            ScoreWidths wd;
+            wd.n = e0.n_widths;
+            for (int k = 0; k < 16; ++k) wd.w[k] = e0.widths[k];
+            if (c.scorer == FFA_SCORE_ALG2)
+                s = launch_score_alg2_group(plane0, c.precision, n, p0s, offs, e0.m_rows, wd, excl, recs, st);
+            else
+                s = launch_score2_group(plane0, c.precision, n, p0s, offs, e0.m_rows, wd, recs, d_status, st);
+            if (s != FFA_OK) return s;
+            t = j;
+        }
+        fold_t.stop();
     }
     return FFA_OK;
 }
@@ -756,7 +1083,7 @@ static ffa_status candidates_range(const ffa_plan* p, int64_t e0, int64_t e1, co
     const int64_t n = el.first_trial + el.m_rows - t0;
     const ffa_record* rec = d_records + t0;
     const float smin = (float)snr_min;
-    const int grid = 152 * 8;
+    const int grid = sm_count() * 8;
     k_cand_init<<<1, 256, 0, st>>>(ctl);
     k_cand_count<<<grid, 256, 0, st>>>(rec, n, smin, ctl);
     for (int pass = 0; pass < 8; ++pass) {
@@ -846,7 +1173,8 @@ ffa_status ffa_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_da
         return fail(FFA_ERR_ARG, "fold: need p0 >= 1, m_rows a power of two >= m_data");
     if (precision != FFA_FOLD_F32 && precision != FFA_FOLD_I8) return fail(FFA_ERR_ARG, "fold: bad precision");
     if (!d_z || !d_plane || !d_tmp) return fail(FFA_ERR_ARG, "fold: null buffer");
-    return launch_fold(d_z, precision, p0, m_data, m_rows, -1, d_plane, d_tmp, as_stream(stream));
+    if (p0 > INT64_MAX / 4 / m_rows) return fail(FFA_ERR_ARG, "fold: m_rows * p0 elements overflow");
+    return launch_fold(d_z, precision, p0, m_data, m_rows, -1, p0, d_plane, d_tmp, as_stream(stream));
 }
 
 ffa_status ffa_score(const void* d_profiles, int32_t precision, int64_t count, int64_t p0,
@@ -864,7 +1192,7 @@ ffa_status ffa_score(const void* d_profiles, int32_t precision, int64_t count, i
     }
     if (count > 0 && (!d_profiles || !d_records)) return fail(FFA_ERR_ARG, "score: null buffer");
     if (precision != FFA_FOLD_F32 && precision != FFA_FOLD_I8) return fail(FFA_ERR_ARG, "score: bad precision");
-    return launch_score2(d_profiles, precision, false, count, 0, p0, 1, wd, d_records, d_status,
+    return launch_score2(d_profiles, precision, false, count, 0, p0, p0, 1, wd, d_records, d_status,
                          as_stream(stream));
 }
 
@@ -884,7 +1212,7 @@ ffa_status ffa_score_alg2(const void* d_profiles, int32_t precision, int64_t cou
     }
     if (count > 0 && (!d_profiles || !d_records)) return fail(FFA_ERR_ARG, "score_alg2: null buffer");
     if (precision != FFA_FOLD_F32 && precision != FFA_FOLD_I8) return fail(FFA_ERR_ARG, "score_alg2: bad precision");
-    return launch_score_alg2(d_profiles, precision, false, count, 0, p0, 1, wd, excl_frac, d_records,
+    return launch_score_alg2(d_profiles, precision, false, count, 0, p0, p0, 1, wd, excl_frac, d_records,
                              as_stream(stream));
 }
 

@@ -86,7 +86,7 @@ extern "C" ffa_status ffa_snr_histogram(const ffa_record* d_records, int64_t n, 
     Edges e;  // by value: no device allocation
     for (int b = 0; b <= n_bins; ++b) e.e[b] = edges[b];
     const int64_t want = (n + HIST_THREADS - 1) / HIST_THREADS;
-    const int grid = (int)std::min<int64_t>(want, 152 * 4);
+    const int grid = (int)std::min<int64_t>(want, (int64_t)sm_count() * 4);
     k_snr_hist<<<grid, HIST_THREADS, 0, st>>>(d_records, n, e, n_bins, (unsigned long long*)d_counts);
     FFA_LAUNCH_CHECK("snr histogram");
     count_launch(1);

@@ -90,11 +90,15 @@ _sig = {
     "ffa_plan_destroy": ([_P], None),
     "ffa_plan_info": ([_P, _P, _P, _P, _P, _P], C.c_int),
     "ffa_plan_entries": ([_P, _P, _i64], C.c_int),
+    "ffa_plan_periods": ([_P, _i64, _i64, _P], C.c_int),
+    "ffa_search_series": ([_P, _P, _i32, _i32, _P, C.c_size_t, _P, _P, _P], C.c_int),
+    "ffa_search_plane": ([_P, _P, _i64, _P, C.c_size_t, _P, _P, _P], C.c_int),
     "ffa_search": ([_P, _P, _P, C.c_size_t, _P, _P, _P], C.c_int),
     "ffa_search_entries": ([_P, _P, _i64, _i64, _P, C.c_size_t, _P, _P, _P], C.c_int),
     "ffa_search_persistence": ([_P, _P, _P, C.c_size_t, _P, _P, _P, _P], C.c_int),
     "ffa_autotune": ([_P, _P, C.c_size_t, _P, _P], C.c_int),
     "ffa_search_batch": ([_P, _P, _i32, _P, C.c_size_t, _P, _P, _P], C.c_int),
+    "ffa_batch_workspace_bytes": ([_P, _i32, _P], C.c_int),
     "ffa_candidates": ([_P, _P, C.c_double, _i32, _P, C.c_size_t, _P, _P, _P, _P, _P, _i32],
                        C.c_int),
     "ffa_candidates_entries": ([_P, _i64, _i64, _P, C.c_double, _i32, _P, C.c_size_t, _P, _P, _P, _P,
@@ -209,13 +213,12 @@ class Plan:
             _lib.ffa_plan_destroy(h)
             self._h = None
 
-    def periods(self) -> np.ndarray:
-        out = []
-        for e in self.entries:
-            m = int(e["m_rows"])
-            scale = self.cfg.tsamp * self.cfg.downsample0 * 2.0 ** int(e["octave"])
-            out.append((e["p0"] + np.arange(m) / (m - 1)) * scale)
-        return np.concatenate(out) if out else np.zeros(0)
+    def periods(self, trial_begin: int = 0, count: int | None = None) -> np.ndarray:
+        """Trial periods in seconds (ffa_plan_periods: Eq. 2, computed by the library)."""
+        count = self.n_trials - trial_begin if count is None else int(count)
+        out = np.zeros(max(count, 0), np.float64)
+        _check(_lib.ffa_plan_periods(self._h, int(trial_begin), count, out.ctypes.data_as(C.c_void_p)))
+        return out
 
     def workspace(self, device=None) -> torch.Tensor:
         dev = device or torch.device("cuda", torch.cuda.current_device())
@@ -280,12 +283,58 @@ def search_entries(plan: Plan, series: torch.Tensor, entry_begin: int, entry_end
     return records
 
 
+DUMP_RESID, DUMP_Z = 0, 1
+
+
+def search_series(plan: Plan, series: torch.Tensor, octave: int, what: int = DUMP_Z,
+                  workspace: torch.Tensor | None = None, status: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """Octave `octave`'s dereddened series (DUMP_RESID, float64) or fold input
+    (DUMP_Z: float32 z, or the int8 code), as the search prepares it."""
+    assert series.is_cuda and series.is_contiguous() and series.numel() == plan.n
+    dev = series.device
+    workspace = plan.workspace(dev) if workspace is None else workspace
+    status = status_word(dev) if status is None else status
+    n_o = int(plan.entries["n_octave"][plan.entries["octave"] == octave][0])
+    dt = torch.float64 if what == DUMP_RESID else (
+        torch.float32 if plan.cfg.precision == FOLD_F32 else torch.int8)
+    out = torch.empty(max(n_o, 1), dtype=dt, device=dev)
+    _check(_lib.ffa_search_series(plan._h, _ptr(series), int(octave), int(what), _ptr(workspace),
+                                  workspace.numel(), _ptr(out), _ptr(status), _stream(stream)))
+    return out[:n_o]
+
+
+def search_plane(plan: Plan, series: torch.Tensor, entry: int, workspace: torch.Tensor | None = None,
+                 status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Every folded profile of plan entry `entry`: an (M, P0) tensor, row k = trial k."""
+    assert series.is_cuda and series.is_contiguous() and series.numel() == plan.n
+    dev = series.device
+    workspace = plan.workspace(dev) if workspace is None else workspace
+    status = status_word(dev) if status is None else status
+    e = plan.entries[int(entry)]
+    dt = torch.float32 if plan.cfg.precision == FOLD_F32 else torch.int32
+    plane = torch.empty((int(e["m_rows"]), int(e["p0"])), dtype=dt, device=dev)
+    _check(_lib.ffa_search_plane(plan._h, _ptr(series), int(entry), _ptr(workspace), workspace.numel(),
+                                 _ptr(plane), _ptr(status), _stream(stream)))
+    return plane
+
+
+def batch_workspace_bytes(plans) -> int:
+    """Workspace bytes ffa_search_batch needs for this batch of plans."""
+    n = len(plans)
+    hp = (C.c_void_p * n)(*[p._h.value for p in plans])
+    b = C.c_size_t()
+    _check(_lib.ffa_batch_workspace_bytes(hp, n, C.byref(b)))
+    return b.value
+
+
 def search_batch(plans, series, workspace: torch.Tensor | None = None, records=None,
                  status: torch.Tensor | None = None, stream=None):
-    """Search a batch of series (uneven lengths), each with its own plan; returns the record tensors."""
+    """Search a batch of series (uneven lengths, one configuration), base periods
+    of all series folded and scored together; returns the record tensors."""
     assert len(plans) == len(series)
     dev = series[0].device
-    need = max(p.workspace_bytes for p in plans)
+    need = batch_workspace_bytes(plans)
     workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev) if workspace is None else workspace
     records = [p.records(dev) for p in plans] if records is None else records
     status = status_word(dev) if status is None else status
@@ -457,14 +506,15 @@ TIMING_SAMPLE = 64  # phases 2/3 time every 64th base period of each octave
 
 
 def timing_read():
-    """Return (ms[4, 64], counts[4, 64]) summed per (phase, octave); clears the record.
+    """Return (ms[6, 64], counts[6, 64]) summed per (phase, octave); clears the record.
 
     Phases: 0 preparation, 1 fold + score, 2 fold launches and 3 scoring launch
-    of every TIMING_SAMPLE-th base period of the octave."""
-    ms = np.zeros(256, np.float64)
-    cnt = np.zeros(256, np.int32)
-    _check(_lib.ffa_timing_read(ms.ctypes.data_as(C.c_void_p), cnt.ctypes.data_as(C.c_void_p), 256))
-    return ms.reshape(4, 64), cnt.reshape(4, 64)
+    of every TIMING_SAMPLE-th base period of the octave, 4 and 5 the same for
+    the groups of short base periods holding one of them."""
+    ms = np.zeros(384, np.float64)
+    cnt = np.zeros(384, np.int32)
+    _check(_lib.ffa_timing_read(ms.ctypes.data_as(C.c_void_p), cnt.ctypes.data_as(C.c_void_p), 384))
+    return ms.reshape(6, 64), cnt.reshape(6, 64)
 
 
 # ---- individual steps --------------------------------------------------------

@@ -127,3 +127,24 @@ def test_server_request_bytes(ffa):
     u8 = ffa.Config(**CONFIGS[0][1], in_type=ffa.IN_U8)
     plan = ffa.Plan(u8, 65536)
     assert ffa.request_bytes(u8, 65536) == al(65536) + al(16 * plan.n_trials) + al(plan.workspace_bytes)
+
+
+def test_plan_periods_eq2():
+    """ffa_plan_periods: Eq. 2 with N = M * P0, written out here from the plan
+    entries; a range in the middle of the periodogram, and bounds errors."""
+    from paper_1703_05581_gb300 import ffa
+    cfg = ffa.Config(tsamp=64e-6, period_min=1.0, period_max=5.0, downsample0=32)
+    plan = ffa.Plan(cfg, 1 << 22)
+    want = []
+    for e in plan.entries:
+        m, p0 = int(e["m_rows"]), int(e["p0"])
+        scale = 64e-6 * 32 * 2.0 ** int(e["octave"])
+        want += [(p0 + k * p0 / (m * p0 - p0)) * scale for k in range(m)]
+    want = np.array(want)
+    got = plan.periods()
+    assert got.size == plan.n_trials
+    np.testing.assert_allclose(got, want, rtol=1e-15)
+    mid = plan.periods(1000, 777)
+    assert np.array_equal(mid, got[1000:1777])
+    with pytest.raises(ffa.FFAError):
+        plan.periods(plan.n_trials - 1, 2)

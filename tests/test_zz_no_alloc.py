@@ -69,3 +69,27 @@ def test_noalloc_fold_rejects_oversized(F):
     st = F._lib.ffa_fold_noalloc(F._ptr(z), F.FOLD_F32, p0, 1, m, F._ptr(z), s)
     assert st == F.ERR_UNSUPPORTED
     assert b"FFA_NOALLOC_FOLD_MAX_ELEMS" in F._lib.ffa_last_error()
+    # m_rows * p0 beyond int64 would wrap in a plain product: still rejected
+    st = F._lib.ffa_fold_noalloc(F._ptr(z), F.FOLD_F32, 1 << 24, 1, 1 << 40, F._ptr(z), s)
+    assert st == F.ERR_UNSUPPORTED
+
+
+def test_noalloc_fold_allocates_nothing(F):
+    """A warm call changes neither the caching allocator's count nor the
+    device's free memory (the output plane is allocated before measuring)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(5)
+    p0, md, m = 1000, 700, 1024
+    z = torch.from_numpy(rng.standard_normal(md * p0).astype(np.float32)).to(dev)
+    first = _fold_noalloc(F, z, F.FOLD_F32, p0, md, m)  # warm: set-up and kernels loaded
+    plane = torch.empty_like(first)
+    torch.cuda.synchronize()
+    alloc0 = torch.cuda.memory_allocated(dev)
+    free0, _ = torch.cuda.mem_get_info(dev)
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    F._check(F._lib.ffa_fold_noalloc(F._ptr(z), F.FOLD_F32, p0, md, m, F._ptr(plane), s))
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated(dev) == alloc0
+    assert torch.cuda.mem_get_info(dev)[0] == free0
+    assert torch.equal(plane, first)
