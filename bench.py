@@ -32,6 +32,8 @@ Other measurements (one JSON line each, not the headline):
   --kernel fold-score [--p0 P --m-data D --m M --widths W] [--reps R]
                                 one base period's fold and scoring, CUDA events
   --kernel search               one whole survey search with per-octave phase times
+  --kernel entry [--entry E]    one base period of the survey through the search's own path
+                                (preparation of its octave, fold passes, fused scorer), 3 times
 """
 from __future__ import annotations
 
@@ -65,7 +67,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=["survey", "plain", "batch", "serve"], default="survey")
-    ap.add_argument("--kernel", choices=["fold-score", "search"], default=None)
+    ap.add_argument("--kernel", choices=["fold-score", "search", "entry"], default=None)
+    ap.add_argument("--entry", type=int, default=4375,
+                    help="--kernel entry: plan entry of the survey (4375: P0 = 20000, M = 4096)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0,
                     help="target CPU seconds of the oracle baseline sample")
@@ -73,7 +77,7 @@ def parse_args():
     # batch
     ap.add_argument("--series", type=int, default=64)
     ap.add_argument("--chunk", type=int, default=64)
-    ap.add_argument("--precision", choices=["f32", "i8"], default="f32")
+    ap.add_argument("--precision", choices=["f32", "i8", "both"], default="f32")
     # serve
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=60.0)
@@ -580,55 +584,77 @@ def run_batch(args):
     from paper_1703_05581_gb300 import ffa
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    prec = ffa.FOLD_F32 if args.precision == "f32" else ffa.FOLD_I8
     xs = [torch.from_numpy(x).to(dev) for x in batch_series(args.series)]
-    plans = [ffa.Plan(ffa.Config(**BATCH_KW, precision=prec), int(x.numel())) for x in xs]
     chunk = max(1, min(args.chunk, len(xs)))
-    units = sum(plan_units(p.entries) for p in plans)
-    in_b = 4 if prec == ffa.FOLD_F32 else 1
-    bytes_alg = sum(search_bytes(p.entries, in_b) for p in plans)
-    ws = torch.empty(max(ffa.batch_workspace_bytes(plans[i:i + chunk]) for i in range(0, len(plans), chunk)),
-                     dtype=torch.uint8, device=dev)
-    n_rec = max(p.n_trials for p in plans)
-    rec_pool = torch.empty((chunk, max(n_rec, 1), 4), dtype=torch.int32, device=dev)
-    recs = [rec_pool[i] for i in range(chunk)]
     st = ffa.status_word(dev)
     stream = torch.cuda.Stream(dev)
-
-    def one_pass():
-        for i in range(0, len(plans), chunk):
-            pp = plans[i:i + chunk]
-            ffa.search_batch(pp, xs[i:i + chunk], workspace=ws, records=recs[:len(pp)], status=st, stream=stream)
-
-    ffa.autotune(plans[0], torch.empty(plans[0].workspace_bytes, dtype=torch.uint8, device=dev), stream=stream)
-    ffa.search_batch(plans[:chunk], xs[:chunk], workspace=ws, records=recs[:min(chunk, len(plans))], status=st,
-                     stream=stream)  # warm-up
-    ffa.wait(st, stream=stream)
-    sampler = ClockSampler(0)
-    sampler.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = ffa.launch_count()
-    e0.record(stream)
-    one_pass()
-    e1.record(stream)
-    e1.synchronize()
-    launches = ffa.launch_count() - l0
-    clocks = sampler.stop()
-    ffa.wait(st, stream=stream)
-    ms = e0.elapsed_time(e1)
     peak, peak_kind = measured_peaks()
-    gbs = bytes_alg / (ms / 1e3) / 1e9
-    print(json.dumps({
-        "metric": METRIC + ", batch", "value": units / (ms / 1e3), "unit": UNIT, "ms": ms,
-        "series": len(xs), "chunk": chunk, "precision": args.precision,
-        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                     "peak_kind": peak_kind, "bytes": bytes_alg,
-                     "bytes_def": f"per base period {in_b}*M_data*P0 + 16*M, plus 16 B per octave sample"},
-        "gpu_launches": int(launches), "clocks": clocks,
-        "config": {"workload": "batch: lengths U[2^22, 2^23] at 512 us, white + AR(1) red noise, 5 % pulsars; "
-                               "0.5-20 s, duty 0.2", "input": "series resident on the device",
-                   "records": f"{chunk} record buffers reused chunk after chunk"},
-    }), flush=True)
+    precs = ["f32", "i8"] if args.precision == "both" else [args.precision]
+    best = {}
+    for pname in precs:
+        prec = ffa.FOLD_F32 if pname == "f32" else ffa.FOLD_I8
+        plans = [ffa.Plan(ffa.Config(**BATCH_KW, precision=prec), int(x.numel())) for x in xs]
+        units = sum(plan_units(p.entries) for p in plans)
+        in_b = 4 if prec == ffa.FOLD_F32 else 1
+        bytes_alg = sum(search_bytes(p.entries, in_b) for p in plans)
+        ws = torch.empty(max(ffa.batch_workspace_bytes(plans[i:i + chunk]) for i in range(0, len(plans), chunk)),
+                         dtype=torch.uint8, device=dev)
+        n_rec = max(p.n_trials for p in plans)
+        rec_pool = torch.empty((chunk, max(n_rec, 1), 4), dtype=torch.int32, device=dev)
+        recs = [rec_pool[i] for i in range(chunk)]
+        best[pname] = []
+
+        def one_pass(keep):
+            for i in range(0, len(plans), chunk):
+                pp = plans[i:i + chunk]
+                ffa.search_batch(pp, xs[i:i + chunk], workspace=ws, records=recs[:len(pp)], status=st,
+                                 stream=stream)
+                if keep:  # best record of each series (untimed pass)
+                    for j, p in enumerate(pp):
+                        snr = recs[j][: p.n_trials, 0].view(torch.float32)
+                        b = int(torch.argmax(snr).item())
+                        best[pname].append((b, float(snr[b].item())))
+
+        ffa.autotune(plans[0], torch.empty(plans[0].workspace_bytes, dtype=torch.uint8, device=dev), stream=stream)
+        ffa.search_batch(plans[:chunk], xs[:chunk], workspace=ws, records=recs[:min(chunk, len(plans))], status=st,
+                         stream=stream)  # warm-up
+        ffa.wait(st, stream=stream)
+        sampler = ClockSampler(0)
+        sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ffa.launch_count()
+        e0.record(stream)
+        one_pass(False)
+        e1.record(stream)
+        e1.synchronize()
+        launches = ffa.launch_count() - l0
+        clocks = sampler.stop()
+        ffa.wait(st, stream=stream)
+        ms = e0.elapsed_time(e1)
+        gbs = bytes_alg / (ms / 1e3) / 1e9
+        line = {
+            "metric": METRIC + ", batch", "value": units / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "series": len(xs), "chunk": chunk, "precision": pname,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_kind": peak_kind, "bytes": bytes_alg,
+                         "bytes_def": f"per base period {in_b}*M_data*P0 + 16*M, plus 16 B per octave sample"},
+            "gpu_launches": int(launches), "clocks": clocks,
+            "config": {"workload": "batch: lengths U[2^22, 2^23] at 512 us, white + AR(1) red noise, 5 % pulsars; "
+                                   "0.5-20 s, duty 0.2", "input": "series resident on the device",
+                       "records": f"{chunk} record buffers reused chunk after chunk"},
+        }
+        if len(precs) == 2 and pname == "i8":
+            one_pass(True)
+            b32 = best["f32"]
+            b8 = best["i8"]
+            same = [a[0] == b[0] for a, b in zip(b32, b8)]
+            d = np.array([abs(a[1] - b[1]) for a, b in zip(b32, b8)])
+            line["int8_vs_fp32"] = {"same_best_trial": float(np.mean(same)),
+                                    "best_snr_abs_diff_median": float(np.median(d)),
+                                    "best_snr_abs_diff_max": float(d.max())}
+        elif len(precs) == 2:
+            one_pass(True)
+        print(json.dumps(line), flush=True)
 
 
 def serve_requests(rate: float, count: int, seed: int, pool: np.ndarray):
@@ -762,6 +788,25 @@ def run_kernel(args):
                           "prep_ms_per_octave": np.round(ms[0][:plan.n_octaves], 3).tolist(),
                           "fold_score_ms_per_octave": np.round(ms[1][:plan.n_octaves], 3).tolist(),
                           "shares": kernel_shares(plan, ms, cnt, 1, (t1 - t0) * 1e3)}), flush=True)
+        return
+    if args.kernel == "entry":
+        kw, n, make, _ = workload("survey")
+        plan = ffa.Plan(ffa.Config(**kw), n)
+        e = plan.entries[args.entry]
+        x = torch.from_numpy(make(2)).to(dev)
+        ws, rec, st = plan.workspace(dev), plan.records(dev), ffa.status_word(dev)
+        ffa.timing_read()
+        ffa.timing_enable(True)
+        for _ in range(3):
+            ffa.search_entries(plan, x, args.entry, args.entry + 1, workspace=ws, records=rec, status=st)
+        ffa.wait(st)
+        ffa.timing_enable(False)
+        ms, cnt = ffa.timing_read()
+        o = int(e["octave"])
+        print(json.dumps({"entry": args.entry, "p0": int(e["p0"]), "m_rows": int(e["m_rows"]),
+                          "m_data": int(e["m_data"]), "octave": o,
+                          "fold_ms": float(ms[2][o] / max(cnt[2][o], 1)), "score_ms": float(ms[3][o] / max(cnt[3][o], 1)),
+                          "bytes_alg": float(entry_bytes(plan.entries[args.entry:args.entry + 1]).sum())}), flush=True)
         return
     shapes = SURVEY_SHAPES if args.p0 is None else [(args.p0, args.m_data, args.m, args.widths)]
     for p0, md, m, nw in shapes:

@@ -92,8 +92,9 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_al
 // offset is its misalignment; the chunk holding the segment's last element
 // ends within that element's 16-byte block, so nothing outside it is read.
 // A wrapping segment (or a row shorter than the segment) is copied element
-// by element at offset 0, int8 rows are widened to int32 through registers,
-// and rows at or beyond m_data (live == false) are zero.
+// by element at offset 0, int8 rows are widened to int32 through registers
+// (whole 4-byte words when the segment does not wrap), and rows at or beyond
+// m_data (live == false) are zero.
 template <class T, class S>
 __device__ __forceinline__ int stage_row(T* __restrict__ rowp, const S* __restrict__ src, int64_t base,
                                          int64_t p0, int wt, bool live, int lane) {
@@ -126,6 +127,22 @@ __device__ __forceinline__ int stage_row(T* __restrict__ rowp, const S* __restri
         }
         return 0;
     } else {
+        if (base + wt <= p0) {
+            // int8 series widened to int32: whole aligned 4-byte words of the
+            // segment, one load per lane per word, each byte sign-extended into
+            // one 128-bit shared store; logical column 0 sits at the segment's
+            // misalignment, as for the copied rows (little-endian bytes)
+            const S* g = src + base;
+            const int a = (int)((uintptr_t)g & 3);
+            const uint32_t* w0 = reinterpret_cast<const uint32_t*>(g - a);
+            const int nw = (wt + a + 3) >> 2;
+            for (int k = lane; k < nw; k += 32) {
+                const uint32_t v = __ldg(w0 + k);
+                *reinterpret_cast<int4*>(rowp + 4 * k) =
+                    make_int4((int)(v << 24) >> 24, (int)(v << 16) >> 24, (int)(v << 8) >> 24, (int)v >> 24);
+            }
+            return a;
+        }
         int64_t col = base + lane;
         while (col >= p0) col -= p0;
         for (int x = lane; x < wt; x += 32) {
@@ -142,7 +159,7 @@ __device__ __forceinline__ int stage_row(T* __restrict__ rowp, const S* __restri
 // registers (compile-time shifts): out[v][0..3] is trial v at the first four
 // columns.  load() reads a row's W values starting at element offset `off`
 // (0..3) of a 16-byte aligned pointer: 128-bit loads, then two branch-free
-// selects per value.
+// selects per value (a warp-uniform branch on the offset measured slower).
 // ---------------------------------------------------------------------------
 template <class T, int QQ>
 struct RegFFA {

@@ -683,7 +683,64 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         fq = fmaf(f, f, fq);
         famax = fmaxf(famax, fabsf(f));
     };
-    if (trow) {
+    if (trow && (ld_ & 3) == 0 && ((uintptr_t)prof & 15) == 0) {
+        // Rows 16-byte aligned (the search's padded planes): 4 bins a thread at
+        // a time, the head row by 128-bit loads, the tail row (read from column
+        // sft on, cyclically) by two aligned 128-bit loads picked at its
+        // misalignment (the same for the whole profile, so the branch is
+        // uniform); the one chunk that straddles the tail's wrap goes element
+        // by element.  Reads past a row's last column stay inside the plane's
+        // pitch or the workspace after it; their values are not used.
+        const int n1 = p0 - sft;  // bins before the tail's wrap
+        const int s_lo = sft & 3, s_hi = (sft - p0) & 3;
+        auto tail4 = [&](int col, int sh, T (&t)[4]) {
+            T a[8];
+            const T* q = trow + (col - sh);
+            *reinterpret_cast<int4*>(&a[0]) = *reinterpret_cast<const int4*>(q);
+            if (sh) *reinterpret_cast<int4*>(&a[4]) = *reinterpret_cast<const int4*>(q + 4);
+            switch (sh) {
+                case 0: t[0] = a[0]; t[1] = a[1]; t[2] = a[2]; t[3] = a[3]; break;
+                case 1: t[0] = a[1]; t[1] = a[2]; t[2] = a[3]; t[3] = a[4]; break;
+                case 2: t[0] = a[2]; t[1] = a[3]; t[2] = a[4]; t[3] = a[5]; break;
+                default: t[0] = a[3]; t[1] = a[4]; t[2] = a[5]; t[3] = a[6]; break;
+            }
+        };
+        const int nq = (p0 + 3) >> 2;
+#pragma unroll 2
+        for (int qq = tid; qq < nq; qq += T2) {
+            const int j0 = 4 * qq;
+            T h[4], t[4];
+            *reinterpret_cast<int4*>(h) = *reinterpret_cast<const int4*>(hrow + j0);
+            if (j0 + 3 < n1) {
+                tail4(j0 + sft, s_lo, t);
+            } else if (j0 >= n1) {
+                tail4(j0 - n1, s_hi, t);
+            } else {
+#pragma unroll
+                for (int c2 = 0; c2 < 4; ++c2) {
+                    const int j = j0 + c2;
+                    t[c2] = j < p0 ? (j < n1 ? trow[j + sft] : trow[j - n1]) : (T)0;
+                }
+            }
+            if (j0 + 3 < p0) {
+                T v[4];
+#pragma unroll
+                for (int c2 = 0; c2 < 4; ++c2) {
+                    v[c2] = h[c2] + t[c2];
+                    acc(v[c2]);
+                }
+                *reinterpret_cast<int4*>(buf + sidx_c<C>(j0)) = *reinterpret_cast<const int4*>(v);
+            } else {
+#pragma unroll
+                for (int c2 = 0; c2 < 4; ++c2)
+                    if (j0 + c2 < p0) {
+                        const T v = h[c2] + t[c2];
+                        buf[sidx_c<C>(j0 + c2)] = v;
+                        acc(v);
+                    }
+            }
+        }
+    } else if (trow) {
         // the tail row read from column sft on: two contiguous runs
         const int n1 = p0 - sft;
 #pragma unroll 4
