@@ -68,8 +68,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=["survey", "plain", "batch", "serve"], default="survey")
     ap.add_argument("--kernel", choices=["fold-score", "search", "entry"], default=None)
-    ap.add_argument("--entry", type=int, default=4375,
-                    help="--kernel entry: plan entry of the survey (4375: P0 = 20000, M = 4096)")
+    ap.add_argument("--entry", type=int, default=4352,
+                    help="--kernel entry: plan entry of the survey (4352: P0 = 19977, M = 4096, one the "
+                         "timing hooks sample)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0,
                     help="target CPU seconds of the oracle baseline sample")
