@@ -205,11 +205,12 @@ ffa_status ffa_search_persistence(const ffa_plan* plan, const void* d_series, vo
                                   int32_t* d_status, void* stream);
 
 /* Autotuner: for every fold shape of the plan (stage count, floor(log2 P0)),
- * time the FFA with at most 3, 4 and 5 stages per HBM pass on its median
- * base period and keep the fastest for every later search on this device
- * (process-wide cache).  The pass depth never changes a result: every split
- * runs the recursion's add tree.  Uses the workspace as scratch; blocks until
- * the timing launches on `stream` finish.  *n_tuned = shapes tuned. */
+ * time the FFA with at most 3, 4, 5 and 6 stages per HBM pass, each with
+ * column tiles of 128 and 256, on its median base period, and keep the
+ * fastest for every later search on this device (process-wide cache).  The
+ * pass depth and the tile width never change a result: every split runs the
+ * recursion's add tree.  Uses the workspace as scratch; blocks until the
+ * timing launches on `stream` finish.  *n_tuned = shapes tuned. */
 ffa_status ffa_autotune(const ffa_plan* plan, void* d_workspace, size_t workspace_bytes, void* stream,
                         int32_t* n_tuned);
 

@@ -236,29 +236,28 @@ __device__ __forceinline__ void store4(T* d, const T (&v)[4], int64_t left, bool
 // so two CTAs fit an SM.
 // ---------------------------------------------------------------------------
 constexpr int FK_THREADS = 256;
-__host__ __device__ constexpr int fk_b(int q) { return q >= 6 ? 128 : 256; }
 __host__ __device__ constexpr int fk_r4(int x) { return (x + 3) & ~3; }
 __host__ __device__ constexpr int fk_max(int a, int b) { return a > b ? a : b; }
-__host__ __device__ constexpr int fk_wt(int q) { return fk_b(q) + (1 << q) - 1; }                  // staged columns
-__host__ __device__ constexpr int fk_w1(int q, int q1) { return fk_b(q) + (1 << q) - (1 << q1); }  // valid after sub-pass 1
+__host__ __device__ constexpr int fk_wt(int q, int b) { return b + (1 << q) - 1; }                  // staged columns
+__host__ __device__ constexpr int fk_w1(int q, int q1, int b) { return b + (1 << q) - (1 << q1); }  // valid after sub-pass 1
 // Row widths (elements) of the two shared buffers: room for the staging
 // copies and for every 128-bit load of the two sub-passes.
-__host__ __device__ constexpr int fk_wa(int q, int q1) {
-    return fk_max(fk_r4(fk_wt(q) + 3), 4 * ((fk_w1(q, q1) + 3) / 4 - 1) + 4 * ((4 + (1 << q1) - 1 + 6) / 4));
+__host__ __device__ constexpr int fk_wa(int q, int q1, int b) {
+    return fk_max(fk_r4(fk_wt(q, b) + 3), 4 * ((fk_w1(q, q1, b) + 3) / 4 - 1) + 4 * ((4 + (1 << q1) - 1 + 6) / 4));
 }
-__host__ __device__ constexpr int fk_wb(int q, int q1) {
-    return fk_max(fk_r4(fk_w1(q, q1)), (fk_b(q) - 4) + 4 * ((((1 << q1) - 1) * ((1 << (q - q1)) - 1)) / 4) +
-                                           4 * ((4 + (1 << (q - q1)) - 1 + 6) / 4));
+__host__ __device__ constexpr int fk_wb(int q, int q1, int b) {
+    return fk_max(fk_r4(fk_w1(q, q1, b)), (b - 4) + 4 * ((((1 << q1) - 1) * ((1 << (q - q1)) - 1)) / 4) +
+                                              4 * ((4 + (1 << (q - q1)) - 1 + 6) / 4));
 }
 
-template <class T, bool FIRST, int Q1, int Q2>
+template <class T, bool FIRST, int Q1, int Q2, int B>
 __global__ void __launch_bounds__(FK_THREADS, 2) k_fold(const void* __restrict__ src_v, T* __restrict__ dst_all,
                                                        const FoldGroup fg, int s) {
     constexpr int q = Q1 + Q2;
     constexpr int rows = 1 << q;
     constexpr int R1 = 1 << Q1, R2 = 1 << Q2;
-    constexpr int B = fk_b(q), WT = fk_wt(q), W1 = fk_w1(q, Q1);
-    constexpr int WA = fk_wa(q, Q1), WB = fk_wb(q, Q1);
+    constexpr int WT = fk_wt(q, B), W1 = fk_w1(q, Q1, B);
+    constexpr int WA = fk_wa(q, Q1, B), WB = fk_wb(q, Q1, B);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int off_a[rows];
     T* bufA = reinterpret_cast<T*>(smem_raw);
@@ -369,43 +368,59 @@ static int64_t group_units(FoldGroup& fg, int64_t m_rows, int rows, int tile) {
     return u;
 }
 
-template <class T, bool FIRST, int Q1, int Q2>
+template <class T, bool FIRST, int Q1, int Q2, int B>
 static ffa_status launch_k(const void* src, T* dst, FoldGroup& fg, int64_t m_rows, int s, cudaStream_t st) {
     constexpr int q = Q1 + Q2;
     constexpr int rows = 1 << q;
-    const size_t smem = sizeof(T) * ((size_t)rows * fk_wa(q, Q1) + (Q2 > 0 ? (size_t)rows * fk_wb(q, Q1) : 0));
-    ffa_status es = ensure_smem((const void*)k_fold<T, FIRST, Q1, Q2>, smem);
+    const size_t smem =
+        sizeof(T) * ((size_t)rows * fk_wa(q, Q1, B) + (Q2 > 0 ? (size_t)rows * fk_wb(q, Q1, B) : 0));
+    ffa_status es = ensure_smem((const void*)k_fold<T, FIRST, Q1, Q2, B>, smem);
     if (es != FFA_OK) return es;
-    const int64_t units = group_units(fg, m_rows, rows, fk_b(q));
+    const int64_t units = group_units(fg, m_rows, rows, B);
     if (units <= 0) return FFA_OK;
     if (units > INT32_MAX) return fail(FFA_ERR_UNSUPPORTED, "fold: plane too large for one launch");
-    k_fold<T, FIRST, Q1, Q2><<<(unsigned)units, FK_THREADS, smem, st>>>(src, dst, fg, s);
+    k_fold<T, FIRST, Q1, Q2, B><<<(unsigned)units, FK_THREADS, smem, st>>>(src, dst, fg, s);
     FFA_LAUNCH_CHECK("k_fold");
     count_launch();
     return FFA_OK;
 }
 
+// Tile width of a pass: `wide` != 0 takes 256 columns, else 128.
+template <class T, bool FIRST, int Q1, int Q2>
+static ffa_status launch_kb(bool wide, const void* src, T* dst, FoldGroup& fg, int64_t m_rows, int s,
+                            cudaStream_t st) {
+    return wide ? launch_k<T, FIRST, Q1, Q2, 256>(src, dst, fg, m_rows, s, st)
+                : launch_k<T, FIRST, Q1, Q2, 128>(src, dst, fg, m_rows, s, st);
+}
+
 template <class T, bool FIRST>
-static ffa_status pass_q(int q, const void* src, T* dst, FoldGroup& fg, int64_t m_rows, int s,
+static ffa_status pass_q(int q, bool wide, const void* src, T* dst, FoldGroup& fg, int64_t m_rows, int s,
                          cudaStream_t st) {
     switch (q) {
-        case 0: return launch_k<T, FIRST, 0, 0>(src, dst, fg, m_rows, s, st);
-        case 1: return launch_k<T, FIRST, 1, 0>(src, dst, fg, m_rows, s, st);
-        case 2: return launch_k<T, FIRST, 2, 0>(src, dst, fg, m_rows, s, st);
-        case 3: return launch_k<T, FIRST, 3, 0>(src, dst, fg, m_rows, s, st);
-        case 4: return launch_k<T, FIRST, 2, 2>(src, dst, fg, m_rows, s, st);
-        case 5: return launch_k<T, FIRST, 3, 2>(src, dst, fg, m_rows, s, st);
-        case 6: return launch_k<T, FIRST, 3, 3>(src, dst, fg, m_rows, s, st);
+        case 0: return launch_kb<T, FIRST, 0, 0>(wide, src, dst, fg, m_rows, s, st);
+        case 1: return launch_kb<T, FIRST, 1, 0>(wide, src, dst, fg, m_rows, s, st);
+        case 2: return launch_kb<T, FIRST, 2, 0>(wide, src, dst, fg, m_rows, s, st);
+        case 3: return launch_kb<T, FIRST, 3, 0>(wide, src, dst, fg, m_rows, s, st);
+        case 4: return launch_kb<T, FIRST, 2, 2>(wide, src, dst, fg, m_rows, s, st);
+        case 5: return launch_kb<T, FIRST, 3, 2>(wide, src, dst, fg, m_rows, s, st);
+        case 6: return launch_kb<T, FIRST, 3, 3>(wide, src, dst, fg, m_rows, s, st);
         default: break;
     }
     return fail(FFA_ERR_ARG, "fold: at most 6 stages per pass");
 }
 
+// The fold's launch shape: at most `qmax` stages per pass, tiles of `tile`
+// columns (0: 256 below six stages, 128 at six, so that two CTAs fit an SM).
+struct FoldShape {
+    int qmax;
+    int tile;
+};
+
 template <class T>
 static ffa_status fold_impl(const void* d_z, FoldGroup& fg, int64_t m_rows, int stages, T* d_plane, T* d_tmp,
-                            cudaStream_t st, int qmax) {
+                            cudaStream_t st, FoldShape fs) {
     int qs[64];
-    int np = split_passes(stages, qmax, qs);
+    int np = split_passes(stages, fs.qmax, qs);
     if (np == 0) {
         // no stage to run: copy the (zero-padded) rows
         np = 1;
@@ -417,8 +432,9 @@ static ffa_status fold_impl(const void* d_z, FoldGroup& fg, int64_t m_rows, int 
     for (int pi = 0; pi < np; ++pi) {
         T* dst = bufs[(np - 1 - pi) & 1];
         const void* src = pi == 0 ? d_z : (const void*)bufs[(np - pi) & 1];
-        ffa_status e = pi == 0 ? pass_q<T, true>(qs[pi], src, dst, fg, m_rows, s, st)
-                               : pass_q<T, false>(qs[pi], src, dst, fg, m_rows, s, st);
+        const bool wide = fs.tile == 256 || (fs.tile == 0 && qs[pi] < 6);
+        ffa_status e = pi == 0 ? pass_q<T, true>(qs[pi], wide, src, dst, fg, m_rows, s, st)
+                               : pass_q<T, false>(qs[pi], wide, src, dst, fg, m_rows, s, st);
         if (e != FFA_OK) return e;
         s += qs[pi];
     }
@@ -426,15 +442,16 @@ static ffa_status fold_impl(const void* d_z, FoldGroup& fg, int64_t m_rows, int 
 }
 
 // ---------------------------------------------------------------------------
-// Stages per pass, tuned.  Any split of the stages into passes gives the
-// same add tree (bit-identical planes); only the time differs.  The cache
-// maps (device, precision, stages, floor(log2 p0)) to the fastest maximum
-// pass depth measured by tune_fold; untuned shapes use 6.
+// Stages per pass and tile width, tuned.  Any split of the stages into passes,
+// and any tile width, gives the same add tree (bit-identical planes); only the
+// time differs.  The cache maps (device, precision, stages, floor(log2 p0)) to
+// the fastest shape measured by tune_fold; untuned shapes use six stages per
+// pass with the default widths.
 // ---------------------------------------------------------------------------
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, int> g_tune;
-constexpr int QMAX_DEFAULT = 6;
+std::map<std::tuple<int, int, int, int>, FoldShape> g_tune;
+constexpr FoldShape SHAPE_DEFAULT = {6, 0};
 
 int log2i(int64_t v) {
     int r = 0;
@@ -442,24 +459,24 @@ int log2i(int64_t v) {
     return r;
 }
 
-int tuned_qmax(int precision, int stages, int64_t p0) {
+FoldShape tuned_shape(int precision, int stages, int64_t p0) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return QMAX_DEFAULT;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SHAPE_DEFAULT;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(std::make_tuple(dev, precision, stages, log2i(p0)));
-    return it == g_tune.end() ? QMAX_DEFAULT : it->second;
+    return it == g_tune.end() ? SHAPE_DEFAULT : it->second;
 }
 }  // namespace
 
 static ffa_status fold_group(const void* d_z, int32_t precision, FoldGroup& fg, int64_t m_rows, int stages,
-                             void* d_plane, void* d_tmp, cudaStream_t st, int qmax) {
+                             void* d_plane, void* d_tmp, cudaStream_t st, FoldShape fs) {
     if (precision == FFA_FOLD_F32)
-        return fold_impl<float>(d_z, fg, m_rows, stages, (float*)d_plane, (float*)d_tmp, st, qmax);
-    return fold_impl<int32_t>(d_z, fg, m_rows, stages, (int32_t*)d_plane, (int32_t*)d_tmp, st, qmax);
+        return fold_impl<float>(d_z, fg, m_rows, stages, (float*)d_plane, (float*)d_tmp, st, fs);
+    return fold_impl<int32_t>(d_z, fg, m_rows, stages, (int32_t*)d_plane, (int32_t*)d_tmp, st, fs);
 }
 
-ffa_status fold_with(const void* d_z, int32_t precision, int64_t p0, int64_t m_data, int64_t m_rows,
-                     int stages, int64_t ld, void* d_plane, void* d_tmp, cudaStream_t st, int qmax) {
+static ffa_status fold_with(const void* d_z, int32_t precision, int64_t p0, int64_t m_data, int64_t m_rows,
+                            int stages, int64_t ld, void* d_plane, void* d_tmp, cudaStream_t st, FoldShape fs) {
     FoldGroup fg;
     fg.n = 1;
     fg.p0[0] = p0;
@@ -467,34 +484,39 @@ ffa_status fold_with(const void* d_z, int32_t precision, int64_t p0, int64_t m_d
     fg.off[0] = 0;
     fg.ld[0] = ld;
     fg.src[0] = d_z;
-    return fold_group(d_z, precision, fg, m_rows, stages, d_plane, d_tmp, st, qmax);
+    return fold_group(d_z, precision, fg, m_rows, stages, d_plane, d_tmp, st, fs);
 }
 
-// Time each maximum pass depth 3..6 on one shape (CUDA events, best of 2
-// after a warm-up) and cache the fastest.  The planes are scratch.
+// Time each maximum pass depth 3..6 with each tile width (128 and 256
+// columns) on one shape (CUDA events, best of 2 after a warm-up) and cache
+// the fastest.  The planes are scratch.
 ffa_status tune_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data, int64_t m_rows,
                      int stages, int64_t ld, void* d_plane, void* d_tmp, cudaStream_t st, int* best_q) {
     cudaEvent_t e0, e1;
     FFA_CUDA_TRY(cudaEventCreate(&e0));
     FFA_CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bq = QMAX_DEFAULT;
+    FoldShape bs = SHAPE_DEFAULT;
     ffa_status s = FFA_OK;
     for (int q = 3; q <= 6 && s == FFA_OK; ++q) {
-        s = fold_with(d_z, precision, p0, m_data, m_rows, stages, ld, d_plane, d_tmp, st, q);  // warm-up
-        float t_q = 1e30f;
-        for (int rep = 0; rep < 2 && s == FFA_OK; ++rep) {
-            cudaEventRecord(e0, st);
-            s = fold_with(d_z, precision, p0, m_data, m_rows, stages, ld, d_plane, d_tmp, st, q);
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess) s = cuda_fail(cudaGetLastError(), "tune_fold");
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            t_q = ms < t_q ? ms : t_q;
-        }
-        if (t_q < best) {
-            best = t_q;
-            bq = q;
+        for (int tile : {128, 256}) {
+            const FoldShape fs = {q, tile};
+            s = fold_with(d_z, precision, p0, m_data, m_rows, stages, ld, d_plane, d_tmp, st, fs);  // warm-up
+            float t_q = 1e30f;
+            for (int rep = 0; rep < 2 && s == FFA_OK; ++rep) {
+                cudaEventRecord(e0, st);
+                s = fold_with(d_z, precision, p0, m_data, m_rows, stages, ld, d_plane, d_tmp, st, fs);
+                cudaEventRecord(e1, st);
+                if (cudaEventSynchronize(e1) != cudaSuccess) s = cuda_fail(cudaGetLastError(), "tune_fold");
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t_q = ms < t_q ? ms : t_q;
+            }
+            if (s != FFA_OK) break;
+            if (t_q < best) {
+                best = t_q;
+                bs = fs;
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -504,9 +526,9 @@ ffa_status tune_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_d
     FFA_CUDA_TRY(cudaGetDevice(&dev));
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[std::make_tuple(dev, precision, stages, log2i(p0))] = bq;
+        g_tune[std::make_tuple(dev, precision, stages, log2i(p0))] = bs;
     }
-    if (best_q) *best_q = bq;
+    if (best_q) *best_q = bs.qmax * 1000 + bs.tile;
     return FFA_OK;
 }
 
@@ -524,7 +546,7 @@ ffa_status launch_fold_group(const void* d_z, int32_t precision, int n, const in
         fg.src[i] = z ? z[i] : d_z;
     }
     return fold_group(d_z, precision, fg, m_rows, stages, d_plane, d_tmp, st,
-                      tuned_qmax(precision, stages, p0[n - 1]));
+                      tuned_shape(precision, stages, p0[n - 1]));
 }
 
 // Run the first `stages` FFA stages (all of them when stages < 0).  With
@@ -536,7 +558,7 @@ ffa_status launch_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m
     while ((1ll << m) < m_rows) ++m;
     if (stages < 0 || stages > m) stages = m;
     return fold_with(d_z, precision, p0, m_data, m_rows, stages, ld, d_plane, d_tmp, st,
-                     tuned_qmax(precision, stages, p0));
+                     tuned_shape(precision, stages, p0));
 }
 
 }  // namespace ffa

@@ -76,8 +76,9 @@ ffa_status launch_fold_group(const void* d_z, int32_t precision, int n, const in
 // One base period; the plane's rows are `ld` elements apart (ld >= p0).
 ffa_status launch_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data,
                        int64_t m_rows, int stages, int64_t ld, void* d_plane, void* d_tmp, cudaStream_t st);
-// Time pass depths 3..6 for one fold shape and cache the fastest (used by
-// every later launch_fold of that precision, stage count and log2 p0).
+// Time pass depths 3..6 with tiles of 128 and 256 columns for one fold shape
+// and cache the fastest (used by every later launch_fold of that precision,
+// stage count and log2 p0); *best_q = depth * 1000 + tile width.
 ffa_status tune_fold(const void* d_z, int32_t precision, int64_t p0, int64_t m_data, int64_t m_rows,
                      int stages, int64_t ld, void* d_plane, void* d_tmp, cudaStream_t st, int* best_q);
 // Algorithm 1 on `count` trials starting at trial0.  fused: d_prof is the

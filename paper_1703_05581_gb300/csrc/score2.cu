@@ -57,42 +57,26 @@ namespace {
 // CTA shapes.  A profile of p0 bins is cut into blocks of R bins, one per
 // thread; T * R >= p0.  Long profiles take 1024-thread CTAs, one per SM;
 // short ones smaller CTAs, several per SM, each on its own profile.  The
-// shape is the first of 256 x 8, 512 x 16, 1024 x 16, 1024 x 20, 1024 x 24,
-// 1024 x 28, 1024 x 32 that fits, so that almost every thread of a long
-// profile holds bins: a thread without bins only waits at the barriers,
-// while the phases' chains are as long as the threads' blocks.
-// Shared memory holds bin j at sidx_c<C>(j) = j + PAD * (j / SB): storage
-// blocks of SB bins (32, or R when R does not divide 32) followed by PAD
-// words, so every thread's block is 16-byte aligned for vector accesses and
-// the blocks of 8 consecutive threads start on distinct bank quads
-// ((SB + PAD) / 4 odd).
+// shape is the first of 256 x 8, 512 x 16, 1024 x 16, 1024 x 32 that fits.
 template <int TH>
 struct Cfg;
 template <>
 struct Cfg<1024> {
-    static constexpr int T = 1024, R = 32, MAXB = 2048, NBK = 2048, CAPM = 1024, MINB = 1, SB = 32, PAD = 4;
+    static constexpr int T = 1024, R = 32, MAXB = 2048, NBK = 2048, CAPM = 1024, MINB = 1;
 };
 template <>
 struct Cfg<512> {
-    static constexpr int T = 512, R = 16, MAXB = 1024, NBK = 1024, CAPM = 512, MINB = 2, SB = 32, PAD = 4;
+    static constexpr int T = 512, R = 16, MAXB = 1024, NBK = 1024, CAPM = 512, MINB = 2;
 };
 template <>
 struct Cfg<256> {
-    static constexpr int T = 256, R = 8, MAXB = 512, NBK = 512, CAPM = 512, MINB = 4, SB = 32, PAD = 4;
+    static constexpr int T = 256, R = 8, MAXB = 512, NBK = 512, CAPM = 512, MINB = 4;
 };
 // 1024 threads of 16 bins: profiles of 8193..16384 bins, which would leave
 // half or more of a 1024 x 32 CTA idle
 struct CMid {
-    static constexpr int T = 1024, R = 16, MAXB = 2048, NBK = 2048, CAPM = 1024, MINB = 1, SB = 32, PAD = 4;
+    static constexpr int T = 1024, R = 16, MAXB = 2048, NBK = 2048, CAPM = 1024, MINB = 1;
 };
-// 1024 threads of R = 20, 24, 28 bins: profiles of 16385..28672 bins
-template <int RR, int PP>
-struct CR {
-    static constexpr int T = 1024, R = RR, MAXB = 2048, NBK = 2048, CAPM = 1024, MINB = 1, SB = RR, PAD = PP;
-};
-using C20 = CR<20, 8>;
-using C24 = CR<24, 4>;
-using C28 = CR<28, 8>;
 using CBig = Cfg<1024>;
 constexpr double KMAD = 1.4826;   // printed after Eq. 4
 
@@ -102,11 +86,9 @@ constexpr double KMAD = 1.4826;   // printed after Eq. 4
     constexpr int NW = T2 / 32;                           \
     (void)T2; (void)R2; (void)MAXB; (void)NBK; (void)CAPM; (void)NW;
 
-// Shared-memory index of bin t (see the CTA shapes above).
-template <class C>
-__host__ __device__ __forceinline__ int sidx_c(int t) {
-    return C::SB == 32 ? t + C::PAD * (t >> 5) : t + C::PAD * (t / C::SB);
-}
+// Shared-memory index of bin t: 4 pad words per 32-bin block keep every block
+// 16-byte aligned (vector loads) and spread blocked accesses over the banks.
+__device__ __forceinline__ int sidx(int t) { return t + 4 * (t >> 5); }
 
 template <class C>
 struct Sh2 {
@@ -467,7 +449,7 @@ __device__ __forceinline__ T small_width(const T (&c)[C::R], const Sh2<C>& sh, c
     const T Town = B::blockdiff(sh, tid + 1, tid);
     constexpr int NC = W < 4 ? 4 : W;  // next block's first values, 128-bit loads
     T cn[NC];
-    const T* nb = buf + sidx_c<C>((tid + 1) * R2);
+    const T* nb = buf + sidx((tid + 1) * R2);
 #pragma unroll
     for (int k = 0; k < NC; k += 4) *reinterpret_cast<int4*>(&cn[k]) = *reinterpret_cast<const int4*>(nb + k);
     T m0 = B::lowest(), m1 = B::lowest();
@@ -485,43 +467,22 @@ __device__ __forceinline__ T small_width(const T (&c)[C::R], const Sh2<C>& sh, c
     return m0 > m1 ? m0 : m1;
 }
 
-// Width w >= R (a multiple of 4): the box at bin R t + r ends at bin
-// R t + r + w, in block t + d at offset r + m (r < R - m) or in block
-// t + d + 1 at offset r + m - R, with d = w / R and m = w % R; m = 0 for the
-// shapes whose R divides 32 (every width w >= R is a multiple of R).
+// Width w >= 32 (multiple of 32): block tid + w/32 at the same offsets.
 template <class T, bool FIND, class C>
 __device__ __forceinline__ T wide_width(const T (&c)[C::R], const Sh2<C>& sh, const T* buf, int tid,
                                         int w, int nvalid, T target, int* first) {
     FFA_CFG_ALIASES
     using B = BoxOps<T>;
+    const int b2 = tid + w / R2;
+    const T D = B::blockdiff(sh, b2, tid);
+    const int o2 = b2 * R2;
     T m = B::lowest();
-    if constexpr (C::SB == 32) {
-        const int b2 = tid + w / R2;
-        const T D = B::blockdiff(sh, b2, tid);
-        const int o2 = b2 * R2;
 #pragma unroll
-        for (int r = 0; r < R2; ++r) {
-            T bx = B::box(D, buf[sidx_c<C>(o2 + r)], c[r]);
-            if (r < nvalid) {
-                m = bx > m ? bx : m;
-                if (FIND && *first < 0 && bx == target) *first = r;
-            }
-        }
-    } else {
-        const int d = w / R2, mr = w - d * R2;
-        const int b2 = tid + d;
-        const T Da = B::blockdiff(sh, b2, tid);
-        const T Db = mr ? B::blockdiff(sh, b2 + 1, tid) : Da;
-        const T* pa = buf + sidx_c<C>(b2 * R2 + mr);
-        const T* pb = buf + sidx_c<C>((b2 + 1) * R2) + mr - R2;
-#pragma unroll
-        for (int r = 0; r < R2; ++r) {
-            const bool hi = r >= R2 - mr;
-            T bx = B::box(hi ? Db : Da, hi ? pb[r] : pa[r], c[r]);
-            if (r < nvalid) {
-                m = bx > m ? bx : m;
-                if (FIND && *first < 0 && bx == target) *first = r;
-            }
+    for (int r = 0; r < R2; ++r) {
+        T bx = B::box(D, buf[sidx(o2 + r)], c[r]);
+        if (r < nvalid) {
+            m = bx > m ? bx : m;
+            if (FIND && *first < 0 && bx == target) *first = r;
         }
     }
     return m;
@@ -537,26 +498,19 @@ __device__ __forceinline__ void upk2(unsigned long long v, float& a, float& b) {
 }
 
 // Wide widths, float profiles, maxima only: the same per-bin arithmetic as
-// wide_width (D + (c2 - c1), each rounded to nearest) on packed pairs; a
-// chunk of 4 bins never straddles the block change (R, w multiples of 4).
+// wide_width (D + (c2 - c1), each rounded to nearest) on packed pairs.
 template <class C>
 __device__ __forceinline__ float wide_width_f32x2(const float (&c)[C::R], const Sh2<C>& sh, const float* buf,
                                                   int tid, int w, int nvalid) {
     FFA_CFG_ALIASES
-    constexpr bool WHOLE = C::SB == 32;  // R divides every width: one block, m = 0
-    const int d = w / R2, mr = WHOLE ? 0 : w - d * R2;
-    const int b2 = tid + d;
-    const float Da = BoxOps<float>::blockdiff(sh, b2, tid);
-    const float Db = (!WHOLE && mr) ? BoxOps<float>::blockdiff(sh, b2 + 1, tid) : Da;
-    const unsigned long long DDa = pk2(Da, Da), DDb = pk2(Db, Db);
-    const float* pa = buf + sidx_c<C>(b2 * R2 + mr);
-    const float* pb = buf + sidx_c<C>((b2 + 1) * R2) + mr - R2;
+    const int b2 = tid + w / R2;
+    const float D = BoxOps<float>::blockdiff(sh, b2, tid);
+    const unsigned long long DD = pk2(D, D);
+    const float* cb = buf + sidx(b2 * R2);
     float m = -INFINITY, ma = -INFINITY;
 #pragma unroll
     for (int r = 0; r < R2; r += 4) {
-        const bool hi = !WHOLE && r >= R2 - mr;
-        const float4 c2 = *reinterpret_cast<const float4*>((hi ? pb : pa) + r);
-        const unsigned long long DD = hi ? DDb : DDa;
+        const float4 c2 = *reinterpret_cast<const float4*>(cb + r);
         unsigned long long s01, s23, b01, b23;
         asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(s01) : "l"(pk2(c2.x, c2.y)), "l"(pk2(c[r], c[r + 1])));
         asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(s23) : "l"(pk2(c2.z, c2.w)), "l"(pk2(c[r + 2], c[r + 3])));
@@ -683,78 +637,21 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         fq = fmaf(f, f, fq);
         famax = fmaxf(famax, fabsf(f));
     };
-    if (trow && (ld_ & 3) == 0 && ((uintptr_t)prof & 15) == 0) {
-        // Rows 16-byte aligned (the search's padded planes): 4 bins a thread at
-        // a time, the head row by 128-bit loads, the tail row (read from column
-        // sft on, cyclically) by two aligned 128-bit loads picked at its
-        // misalignment (the same for the whole profile, so the branch is
-        // uniform); the one chunk that straddles the tail's wrap goes element
-        // by element.  Reads past a row's last column stay inside the plane's
-        // pitch or the workspace after it; their values are not used.
-        const int n1 = p0 - sft;  // bins before the tail's wrap
-        const int s_lo = sft & 3, s_hi = (sft - p0) & 3;
-        auto tail4 = [&](int col, int sh, T (&t)[4]) {
-            T a[8];
-            const T* q = trow + (col - sh);
-            *reinterpret_cast<int4*>(&a[0]) = *reinterpret_cast<const int4*>(q);
-            if (sh) *reinterpret_cast<int4*>(&a[4]) = *reinterpret_cast<const int4*>(q + 4);
-            switch (sh) {
-                case 0: t[0] = a[0]; t[1] = a[1]; t[2] = a[2]; t[3] = a[3]; break;
-                case 1: t[0] = a[1]; t[1] = a[2]; t[2] = a[3]; t[3] = a[4]; break;
-                case 2: t[0] = a[2]; t[1] = a[3]; t[2] = a[4]; t[3] = a[5]; break;
-                default: t[0] = a[3]; t[1] = a[4]; t[2] = a[5]; t[3] = a[6]; break;
-            }
-        };
-        const int nq = (p0 + 3) >> 2;
-#pragma unroll 2
-        for (int qq = tid; qq < nq; qq += T2) {
-            const int j0 = 4 * qq;
-            T h[4], t[4];
-            *reinterpret_cast<int4*>(h) = *reinterpret_cast<const int4*>(hrow + j0);
-            if (j0 + 3 < n1) {
-                tail4(j0 + sft, s_lo, t);
-            } else if (j0 >= n1) {
-                tail4(j0 - n1, s_hi, t);
-            } else {
-#pragma unroll
-                for (int c2 = 0; c2 < 4; ++c2) {
-                    const int j = j0 + c2;
-                    t[c2] = j < p0 ? (j < n1 ? trow[j + sft] : trow[j - n1]) : (T)0;
-                }
-            }
-            if (j0 + 3 < p0) {
-                T v[4];
-#pragma unroll
-                for (int c2 = 0; c2 < 4; ++c2) {
-                    v[c2] = h[c2] + t[c2];
-                    acc(v[c2]);
-                }
-                *reinterpret_cast<int4*>(buf + sidx_c<C>(j0)) = *reinterpret_cast<const int4*>(v);
-            } else {
-#pragma unroll
-                for (int c2 = 0; c2 < 4; ++c2)
-                    if (j0 + c2 < p0) {
-                        const T v = h[c2] + t[c2];
-                        buf[sidx_c<C>(j0 + c2)] = v;
-                        acc(v);
-                    }
-            }
-        }
-    } else if (trow) {
+    if (trow) {
         // the tail row read from column sft on: two contiguous runs
         const int n1 = p0 - sft;
 #pragma unroll 4
         for (int j = tid; j < p0; j += T2) {
             const T t = j < n1 ? trow[j + sft] : trow[j - n1];
             const T v = hrow[j] + t;
-            buf[sidx_c<C>(j)] = v;
+            buf[sidx(j)] = v;
             acc(v);
         }
     } else {
 #pragma unroll 4
         for (int j = tid; j < p0; j += T2) {
             const T v = hrow[j];
-            buf[sidx_c<C>(j)] = v;
+            buf[sidx(j)] = v;
             acc(v);
         }
     }
@@ -766,7 +663,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     int nvalid = p0 - base_pos;
     nvalid = nvalid < 0 ? 0 : (nvalid > R2 ? R2 : nvalid);
     {
-        const T* blk = buf + sidx_c<C>(base_pos);
+        const T* blk = buf + sidx(base_pos);
 #pragma unroll
         for (int r = 0; r < R2; r += 4) {
             T v4[4];
@@ -861,8 +758,8 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         } else {
             const T* vb = buf;
             auto key = [vb](int j) -> uint64_t {
-                if constexpr (Traits<T>::is_int) return (uint64_t)ikey((int32_t)vb[sidx_c<C>(j)]);
-                else return (uint64_t)fkey((float)vb[sidx_c<C>(j)]);
+                if constexpr (Traits<T>::is_int) return (uint64_t)ikey((int32_t)vb[sidx(j)]);
+                else return (uint64_t)fkey((float)vb[sidx(j)]);
             };
             mka = smem_select64(sh, p0, r1, key);
             mkb = (r1 == r2) ? mka : smem_select64(sh, p0, r2, key);
@@ -1149,7 +1046,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         } else {
             const T* vb = buf;
             auto key = [vb, s2](int j) -> uint64_t {
-                const int e = 2 * (int)vb[sidx_c<C>(j)] - s2;
+                const int e = 2 * (int)vb[sidx(j)] - s2;
                 return (uint64_t)(uint32_t)(e < 0 ? -e : e);
             };
             mk1 = smem_select64(sh, p0, r1, key);
@@ -1201,7 +1098,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         } else {
             if (cc <= CAPM) dev_fail(d_status, FFA_ERR_DEVICE);  // bracket invariant broken
             const T* vb = buf;
-            auto key = [vb, med](int j) -> uint64_t { return dkey(fabs((double)vb[sidx_c<C>(j)] - med)); };
+            auto key = [vb, med](int j) -> uint64_t { return dkey(fabs((double)vb[sidx(j)] - med)); };
             mk1 = smem_select64(sh, p0, r1, key);
             mk2 = (r1 == r2) ? mk1 : smem_select64(sh, p0, r2, key);
         }
@@ -1221,8 +1118,8 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
 #pragma unroll 4
         for (int r = 0; r < R2; ++r) {
             const int j = eb2 * R2 + r;
-            const T v = buf[sidx_c<C>(one_wrap ? j - p0 : j % p0)];
-            buf[sidx_c<C>(eb2 * R2 + r)] = tot2;
+            const T v = buf[sidx(one_wrap ? j - p0 : j % p0)];
+            buf[sidx(eb2 * R2 + r)] = tot2;
             tot2 = tot2 + v;
         }
     }
@@ -1230,13 +1127,13 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     for (int r = 0; r < R2; ++r) {
         const int j = base_pos + r;
         T v = x[r];
-        if (j >= p0) v = (tid < nbe) ? buf[sidx_c<C>(one_wrap ? j - p0 : j % p0)] : (T)0;
+        if (j >= p0) v = (tid < nbe) ? buf[sidx(one_wrap ? j - p0 : j % p0)] : (T)0;
         x[r] = tot;  // exclusive in-block prefix
         tot = tot + v;
     }
     __syncthreads();  // every value read: own blocks now take the prefixes
     {
-        T* blk = buf + sidx_c<C>(base_pos);
+        T* blk = buf + sidx(base_pos);
 #pragma unroll
         for (int r = 0; r < R2; r += 4) *reinterpret_cast<int4*>(blk + r) = *reinterpret_cast<const int4*>(&x[r]);
     }
@@ -1441,7 +1338,7 @@ __device__ __forceinline__ T box_at(const T (&c)[C::R], const Sh2<C>& sh, const 
     // cyclic box of width w starting at bin 32 tid + r, from the blocked prefix
     const int j2 = tid * R2 + r + w;
     const int b2 = j2 / R2, o2 = j2 % R2;
-    return B::box(B::blockdiff(sh, b2, tid), buf[sidx_c<C>(b2 * R2 + o2)], c[r]);
+    return B::box(B::blockdiff(sh, b2, tid), buf[sidx(b2 * R2 + o2)], c[r]);
 }
 
 template <class C, class T, bool FUSED>
@@ -1480,9 +1377,9 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
         }
         if (trow) {
             const int n1 = p0 - sft;
-            for (int j = tid; j < p0; j += T2) buf[sidx_c<C>(j)] = hrow[j] + (j < n1 ? trow[j + sft] : trow[j - n1]);
+            for (int j = tid; j < p0; j += T2) buf[sidx(j)] = hrow[j] + (j < n1 ? trow[j + sft] : trow[j - n1]);
         } else {
-            for (int j = tid; j < p0; j += T2) buf[sidx_c<C>(j)] = hrow[j];
+            for (int j = tid; j < p0; j += T2) buf[sidx(j)] = hrow[j];
         }
         __syncthreads();
         T x[R2];
@@ -1492,7 +1389,7 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
         float fs = 0.0f, fq = 0.0f, fm = 0.0f;
 #pragma unroll
         for (int r = 0; r < R2; ++r) {
-            x[r] = (r < nvalid) ? buf[sidx_c<C>(base_pos + r)] : (T)0;
+            x[r] = (r < nvalid) ? buf[sidx(base_pos + r)] : (T)0;
             if (r < nvalid) fs += (float)x[r];
         }
         blk_stats(fs, fq, fm, sh);
@@ -1514,8 +1411,8 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
         if (eb2 < nbe) {
             for (int r = 0; r < R2; ++r) {
                 const int j = eb2 * R2 + r;
-                const T v = buf[sidx_c<C>(one_wrap ? j - p0 : j % p0)];
-                buf[sidx_c<C>(j)] = tot2;
+                const T v = buf[sidx(one_wrap ? j - p0 : j % p0)];
+                buf[sidx(j)] = tot2;
                 tot2 = tot2 + v;
             }
         }
@@ -1523,13 +1420,13 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score_alg2(const T* __restric
         for (int r = 0; r < R2; ++r) {
             const int j = base_pos + r;
             T v = x[r];
-            if (j >= p0) v = (tid < nbe) ? buf[sidx_c<C>(one_wrap ? j - p0 : j % p0)] : (T)0;
+            if (j >= p0) v = (tid < nbe) ? buf[sidx(one_wrap ? j - p0 : j % p0)] : (T)0;
             x[r] = tot;
             tot = tot + v;
         }
         __syncthreads();
         {
-            T* blk = buf + sidx_c<C>(base_pos);
+            T* blk = buf + sidx(base_pos);
 #pragma unroll
             for (int r = 0; r < R2; r += 4) *reinterpret_cast<int4*>(blk + r) = *reinterpret_cast<const int4*>(&x[r]);
         }
@@ -1710,7 +1607,7 @@ template <class C>
 size_t score2_smem_bytes(int64_t p0, int wmax, size_t elem) {
     const int64_t nbe = (p0 + wmax + C::R) / C::R + 1;
     const int64_t nbins = (nbe > C::T ? nbe : C::T) * C::R + C::R;
-    return ((sizeof(Sh2<C>) + 15) & ~(size_t)15) + (size_t)(sidx_c<C>((int)nbins) + 64) * elem;
+    return ((sizeof(Sh2<C>) + 15) & ~(size_t)15) + (size_t)(nbins + 4 * (nbins / 32) + 64) * elem;
 }
 
 // does a profile of p0 bins with widths up to wmax fit configuration C?
@@ -1753,29 +1650,19 @@ ffa_status launch_score2_t(const void* d_prof, const ScoreGroup& sg, int64_t cou
         return launch_score2_cfg<Cfg<512>, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
     if (fits<CMid>(p0, wmax))
         return launch_score2_cfg<CMid, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
-    if (fits<C20>(p0, wmax))
-        return launch_score2_cfg<C20, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
-    if (fits<C24>(p0, wmax))
-        return launch_score2_cfg<C24, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
-    if (fits<C28>(p0, wmax))
-        return launch_score2_cfg<C28, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
     return launch_score2_cfg<CBig, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, d_rec, d_status, st);
 }
 
 }  // namespace
 
 // The scorer's CTA shape for a profile of p0 bins (0: 256 x 8, 1: 512 x 16,
-// 2: 1024 x 16, 3..5: 1024 x 20, 24, 28, 6: 1024 x 32); grouped launches hold
-// one shape only, so a
+// 2: 1024 x 16, 3: 1024 x 32); grouped launches hold one shape only, so a
 // profile's record does not depend on what it is grouped with.
 int score_shape(int64_t p0, int wmax) {
     if (fits<Cfg<256>>(p0, wmax)) return 0;
     if (fits<Cfg<512>>(p0, wmax)) return 1;
     if (fits<CMid>(p0, wmax)) return 2;
-    if (fits<C20>(p0, wmax)) return 3;
-    if (fits<C24>(p0, wmax)) return 4;
-    if (fits<C28>(p0, wmax)) return 5;
-    return 6;
+    return 3;
 }
 
 namespace {
@@ -1869,12 +1756,6 @@ ffa_status launch_alg2_t(const void* d_prof, const ScoreGroup& sg, int64_t count
         return launch_alg2_cfg<Cfg<512>, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
     if (fits<CMid>(p0, wmax))
         return launch_alg2_cfg<CMid, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
-    if (fits<C20>(p0, wmax))
-        return launch_alg2_cfg<C20, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
-    if (fits<C24>(p0, wmax))
-        return launch_alg2_cfg<C24, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
-    if (fits<C28>(p0, wmax))
-        return launch_alg2_cfg<C28, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
     return launch_alg2_cfg<CBig, TT, FF>(d_prof, sg, count, trial0, p0, m_rows, wd, excl_frac, d_rec, st);
 }
 

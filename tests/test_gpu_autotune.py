@@ -1,5 +1,5 @@
-"""The fold autotuner (stages per HBM pass): tuning changes no result, only
-the time; searches before and after tuning give identical periodograms."""
+"""The fold autotuner (stages per HBM pass and column-tile width): tuning changes no
+result, only the time; searches before and after tuning give identical periodograms."""
 import numpy as np
 import pytest
 
