@@ -548,9 +548,11 @@ def run_gpu(args):
 
 
 # DRAM bytes (read + write) per folded-profile bin of one base period's fold
-# and scoring launches, from an ncu capture of P0 = 20 000, M = 4096 (None
-# until the current kernels are captured).
-DRAM_BYTES_PER_BIN = None
+# and scoring launches on the search's own path: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of the two fold passes and the scorer of survey entry
+# 4352 (P0 = 19977, M = 4096; bench.py --kernel entry), 1474.7 MB over
+# 4096 x 19977 bins.
+DRAM_BYTES_PER_BIN = 1474.7e6 / (4096 * 19977)
 
 
 # ---------------------------------------------------------------------------
