@@ -71,7 +71,7 @@ def parse_args():
     ap.add_argument("--kernel", choices=["fold-score", "search", "entry"], default=None)
     ap.add_argument("--entry", type=int, default=4352,
                     help="--kernel entry: plan entry of the survey (4352: P0 = 19977, M = 4096, one the "
-                         "timing hooks sample)")
+                         "timing hooks sample), or of one DM-trial series with --workload batch")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-budget-s", type=float, default=20.0,
                     help="target CPU seconds of the oracle baseline sample")
@@ -79,7 +79,8 @@ def parse_args():
     # batch
     ap.add_argument("--series", type=int, default=64)
     ap.add_argument("--chunk", type=int, default=64)
-    ap.add_argument("--precision", choices=["f32", "i8", "both"], default="f32")
+    ap.add_argument("--precision", choices=["f32", "i8", "both"], default="f32",
+                    help="batch: fold precision (both: FP32 then int8); --kernel entry: f32 or i8")
     # serve
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=60.0)
@@ -794,10 +795,16 @@ def run_kernel(args):
                           "shares": kernel_shares(plan, ms, cnt, 1, (t1 - t0) * 1e3)}), flush=True)
         return
     if args.kernel == "entry":
-        kw, n, make, _ = workload("survey")
-        plan = ffa.Plan(ffa.Config(**kw), n)
+        prec = ffa.FOLD_I8 if args.precision == "i8" else ffa.FOLD_F32
+        if args.workload == "batch":  # one series of the DM-trial batch recipe
+            xh = next(batch_series(1))
+            plan = ffa.Plan(ffa.Config(**BATCH_KW, precision=prec), xh.size)
+        else:
+            kw, n, make, _ = workload("survey")
+            plan = ffa.Plan(ffa.Config(**kw, precision=prec), n)
+            xh = make(2)
         e = plan.entries[args.entry]
-        x = torch.from_numpy(make(2)).to(dev)
+        x = torch.from_numpy(xh).to(dev)
         ws, rec, st = plan.workspace(dev), plan.records(dev), ffa.status_word(dev)
         ffa.search_entries(plan, x, args.entry, args.entry + 1, workspace=ws, records=rec, status=st)
         ffa.wait(st)  # first call: launch set-up outside the timed calls
@@ -809,10 +816,14 @@ def run_kernel(args):
         ffa.timing_enable(False)
         ms, cnt = ffa.timing_read()
         o = int(e["octave"])
-        print(json.dumps({"entry": args.entry, "p0": int(e["p0"]), "m_rows": int(e["m_rows"]),
+        print(json.dumps({"workload": "batch" if args.workload == "batch" else "survey", "entry": args.entry,
+                          "precision": "i8" if prec == ffa.FOLD_I8 else "f32",
+                          "p0": int(e["p0"]), "m_rows": int(e["m_rows"]),
                           "m_data": int(e["m_data"]), "octave": o,
                           "fold_ms": float(ms[2][o] / max(cnt[2][o], 1)), "score_ms": float(ms[3][o] / max(cnt[3][o], 1)),
-                          "bytes_alg": float(entry_bytes(plan.entries[args.entry:args.entry + 1]).sum())}), flush=True)
+                          "bytes_alg": float(entry_bytes(plan.entries[args.entry:args.entry + 1],
+                                                         1 if prec == ffa.FOLD_I8 else 4).sum())}),
+              flush=True)
         return
     shapes = SURVEY_SHAPES if args.p0 is None else [(args.p0, args.m_data, args.m, args.widths)]
     for p0, md, m, nw in shapes:

@@ -277,18 +277,77 @@ __global__ void __launch_bounds__(FK_THREADS, 2) k_fold(const void* __restrict__
     constexpr int NW = FK_THREADS / 32;
 
     const int64_t kmod = kappa % p0;
-    for (int u = warp; u < rows; u += NW) {
-        const int64_t g = blk * rows + u;
+    auto row_base = [&](int u) -> int64_t {
         int64_t base = c + (kmod * (u % p0)) % p0;
-        if (base >= p0) base -= p0;
-        int a;
-        if (FIRST)
-            a = stage_row(bufA + u * WA, (const typename FoldIn<T>::type*)fg.src[ei] + g * p0, base, p0, WT,
-                          g < m_data, lane);
-        else
-            a = stage_row(bufA + u * WA, (const T*)src_v + fg.off[ei] + ((g << s) + kappa) * ld, base, p0, WT, true,
-                          lane);
-        if (lane == 0) off_a[u] = a;
+        return base >= p0 ? base - p0 : base;
+    };
+    if constexpr (FIRST && sizeof(typename FoldIn<T>::type) == 1) {
+        // int8 series: the plain loads of all of this warp's rows are issued
+        // before any is widened and stored, so that their DRAM latencies
+        // overlap (cp.async cannot widen).  Rows that wrap or lie beyond the
+        // data take stage_row's general path.
+        using S = typename FoldIn<T>::type;
+        constexpr int RPW = (rows + NW - 1) / NW;     // rows per warp
+        constexpr int KPL = ((WT + 6) / 4 + 31) / 32;  // aligned words per lane and row
+        const S* srcb = (const S*)fg.src[ei];
+        uint32_t wv[RPW][KPL];
+        int aw[RPW];
+#pragma unroll
+        for (int j = 0; j < RPW; ++j) {
+            const int u = warp + j * NW;
+            aw[j] = -1;
+            if (u < rows) {
+                const int64_t g = blk * rows + u;
+                const int64_t base = row_base(u);
+                if (g < m_data && base + WT <= p0) {
+                    const S* gp = srcb + g * p0 + base;
+                    const int a = (int)((uintptr_t)gp & 3);
+                    const uint32_t* w0 = reinterpret_cast<const uint32_t*>(gp - a);
+                    const int nw = (WT + a + 3) >> 2;  // the word holding the last element ends the copy
+#pragma unroll
+                    for (int t = 0; t < KPL; ++t) {
+                        const int k = lane + 32 * t;
+                        wv[j][t] = k < nw ? __ldg(w0 + k) : 0u;
+                    }
+                    aw[j] = a;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < RPW; ++j) {
+            const int u = warp + j * NW;
+            if (u >= rows) continue;
+            T* rowp = bufA + u * WA;
+            int a = aw[j];
+            if (a >= 0) {
+                const int nw = (WT + a + 3) >> 2;
+#pragma unroll
+                for (int t = 0; t < KPL; ++t) {
+                    const int k = lane + 32 * t;
+                    const uint32_t v = wv[j][t];
+                    if (k < nw)
+                        *reinterpret_cast<int4*>(rowp + 4 * k) = make_int4(
+                            (int)(v << 24) >> 24, (int)(v << 16) >> 24, (int)(v << 8) >> 24, (int)v >> 24);
+                }
+            } else {
+                const int64_t g = blk * rows + u;
+                a = stage_row(rowp, srcb + g * p0, row_base(u), p0, WT, g < m_data, lane);
+            }
+            if (lane == 0) off_a[u] = a;
+        }
+    } else {
+        for (int u = warp; u < rows; u += NW) {
+            const int64_t g = blk * rows + u;
+            const int64_t base = row_base(u);
+            int a;
+            if (FIRST)
+                a = stage_row(bufA + u * WA, (const typename FoldIn<T>::type*)fg.src[ei] + g * p0, base, p0, WT,
+                              g < m_data, lane);
+            else
+                a = stage_row(bufA + u * WA, (const T*)src_v + fg.off[ei] + ((g << s) + kappa) * ld, base, p0, WT,
+                              true, lane);
+            if (lane == 0) off_a[u] = a;
+        }
     }
     cp_async_wait();
     __syncthreads();

@@ -63,19 +63,23 @@ struct Cfg;
 template <>
 struct Cfg<1024> {
     static constexpr int T = 1024, R = 32, MAXB = 2048, NBK = 2048, CAPM = 1024, MINB = 1;
+    static constexpr bool DIST = true;  // int profiles only (see k_score2)
 };
 template <>
 struct Cfg<512> {
     static constexpr int T = 512, R = 16, MAXB = 1024, NBK = 1024, CAPM = 512, MINB = 2;
+    static constexpr bool DIST = false;
 };
 template <>
 struct Cfg<256> {
     static constexpr int T = 256, R = 8, MAXB = 512, NBK = 512, CAPM = 512, MINB = 4;
+    static constexpr bool DIST = false;
 };
 // 1024 threads of 16 bins: profiles of 8193..16384 bins, which would leave
 // half or more of a 1024 x 32 CTA idle
 struct CMid {
     static constexpr int T = 1024, R = 16, MAXB = 2048, NBK = 2048, CAPM = 1024, MINB = 1;
+    static constexpr bool DIST = false;
 };
 using CBig = Cfg<1024>;
 constexpr double KMAD = 1.4826;   // printed after Eq. 4
@@ -118,6 +122,7 @@ struct Sh2 {
     float bw_maxf[16];         // per-width block maxima (float profiles)
     int bin_a, bin_b;
     uint32_t below_a, below_b;
+    uint32_t wkey[16];  // per-width maxima as order-preserving keys (item-distributed widths)
     int phase;
 };
 
@@ -475,14 +480,19 @@ __device__ __forceinline__ T wide_width(const T (&c)[C::R], const Sh2<C>& sh, co
     using B = BoxOps<T>;
     const int b2 = tid + w / R2;
     const T D = B::blockdiff(sh, b2, tid);
-    const int o2 = b2 * R2;
+    const T* cb = buf + sidx(b2 * R2);  // block b2's bins are contiguous, 16-byte aligned
     T m = B::lowest();
 #pragma unroll
-    for (int r = 0; r < R2; ++r) {
-        T bx = B::box(D, buf[sidx(o2 + r)], c[r]);
-        if (r < nvalid) {
-            m = bx > m ? bx : m;
-            if (FIND && *first < 0 && bx == target) *first = r;
+    for (int r = 0; r < R2; r += 4) {
+        T c2[4];
+        *reinterpret_cast<int4*>(c2) = *reinterpret_cast<const int4*>(cb + r);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const T bx = B::box(D, c2[i], c[r + i]);
+            if (r + i < nvalid) {
+                m = bx > m ? bx : m;
+                if (FIND && *first < 0 && bx == target) *first = r + i;
+            }
         }
     }
     return m;
@@ -856,18 +866,32 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
             }
             __syncthreads();
             if (sh.mok) {
-                const long long l1 = sh.mthri[0], h1 = sh.mthri[1], l2 = sh.mthri[2], h2 = sh.mthri[3];
+                // The profile values are int32, so each interval [lo, hi] is
+                // applied as the int32 interval it contains (empty when it
+                // holds no int32): the same classification in 32-bit compares.
+                int l1, h1, l2, h2;
+                auto narrow = [](long long lo, long long hi, int& l, int& h) {
+                    if (lo > hi || lo > INT32_MAX || hi < INT32_MIN) {
+                        l = 1;
+                        h = 0;
+                    } else {
+                        l = lo < INT32_MIN ? INT32_MIN : (int)lo;
+                        h = hi > INT32_MAX ? INT32_MAX : (int)hi;
+                    }
+                };
+                narrow(sh.mthri[0], sh.mthri[1], l1, h1);
+                narrow(sh.mthri[2], sh.mthri[3], l2, h2);
                 uint32_t nbel = 0;
                 if (nvalid > 0) {
 #pragma unroll
                     for (int r = 0; r < R2; ++r)
                         if (r < nvalid) {
-                            const long long v = (long long)x[r];
+                            const int v = (int)x[r];
                             if (v >= l1 && v <= h1) {
                                 ++nbel;
                             } else if (v >= l2 && v <= h2) {
                                 const uint32_t q = atomicAdd(&sh.cnt, 1u);
-                                const long long e = 2 * v - s2;
+                                const long long e = 2 * (long long)v - s2;
                                 if (q < CAPM) sh.cand[q] = (unsigned long long)(e < 0 ? -e : e);
                             }
                         }
@@ -1131,6 +1155,9 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
         x[r] = tot;  // exclusive in-block prefix
         tot = tot + v;
     }
+    if constexpr (C::DIST && Traits<T>::is_int) {
+        if (tid < 16) sh.wkey[tid] = 0u;  // below every key
+    }
     __syncthreads();  // every value read: own blocks now take the prefixes
     {
         T* blk = buf + sidx(base_pos);
@@ -1201,26 +1228,82 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     // at bin i (i mod p0 for profiles shorter than a block).
     const bool own = base_pos < p0;
     int dummy = -1;
-    for (int wi = 0; wi < wd.n; ++wi) {
-        T m = B::lowest();
-        if (own) m = width_max<T, false>(x, sh, buf, tid, wd.w[wi], R2, (T)0, &dummy);
-        if constexpr (Traits<T>::is_int) {
-            m = warp_maxi(m);
-            if (lane == 0) sh.wredi[wi][warp] = m;
-        } else {
-            m = warp_max(m);
-            if (lane == 0) sh.wred[wi][warp] = m;
+    if constexpr (C::DIST && Traits<T>::is_int) {
+        // Item-distributed widths: item i = (width i / nblk, block i mod
+        // nblk) over every thread of the CTA, each block's in-block prefix
+        // read back from shared memory (the blocks with bins are only part of
+        // the CTA for most profile lengths, and the registers that held the
+        // profile are free again).  A warp's 32 consecutive items span at
+        // most a few widths; each width's warp maximum goes to a shared
+        // order-preserving key by one atomicMax.  Taken for int profiles of
+        // the 1024 x 32 shape, whose register-held widths spill; for float
+        // profiles the per-width re-read of each block costs more shared-
+        // memory bandwidth than the idle threads save (measured).
+        const int nblk = (p0 + R2 - 1) / R2;
+        const int total = wd.n * nblk;
+        const float inv = 1.0f / (float)nblk;
+        for (int i0 = warp * 32; i0 < total; i0 += T2) {
+            const int i = i0 + lane;
+            const bool valid = i < total;
+            int wi = -1;
+            uint32_t key = 0u;
+            if (valid) {
+                wi = (int)((float)i * inv);  // floor(i / nblk) up to one step
+                int b = i - wi * nblk;
+                if (b < 0) {
+                    --wi;
+                    b += nblk;
+                } else if (b >= nblk) {
+                    ++wi;
+                    b -= nblk;
+                }
+                T c[R2];
+                const T* cb = buf + sidx(b * R2);
+#pragma unroll
+                for (int r = 0; r < R2; r += 4)
+                    *reinterpret_cast<int4*>(&c[r]) = *reinterpret_cast<const int4*>(cb + r);
+                const T m = width_max<T, false>(c, sh, buf, b, wd.w[wi], R2, (T)0, &dummy);
+                if constexpr (Traits<T>::is_int) key = ikey((int32_t)m);
+                else key = fkey((float)m);
+            }
+            unsigned pend = __ballot_sync(0xffffffffu, valid);
+            while (pend) {
+                const int src = __ffs(pend) - 1;
+                const int wa = __shfl_sync(0xffffffffu, wi, src);
+                const bool mine = valid && wi == wa;
+                const uint32_t km = __reduce_max_sync(0xffffffffu, mine ? key : 0u);
+                if (lane == src) atomicMax(&sh.wkey[wa], km);
+                pend &= ~__ballot_sync(0xffffffffu, mine);
+            }
         }
-    }
-    __syncthreads();
-    // per-width block maxima: warp w reduces the warp maxima of widths w, w + NW, ...
-    for (int wi = warp; wi < wd.n; wi += NW) {
-        if constexpr (Traits<T>::is_int) {
-            const double Bw = (double)warp_maxi(lane < NW ? sh.wredi[wi][lane] : INT32_MIN);
-            if (lane == 0) sh.bw_max[wi] = Bw;
-        } else {
-            const float bf = warp_max(lane < NW ? sh.wred[wi][lane] : -INFINITY);
-            if (lane == 0) sh.bw_maxf[wi] = bf;
+        __syncthreads();
+        if (tid < wd.n) {
+            const uint32_t k = sh.wkey[tid];
+            if constexpr (Traits<T>::is_int) sh.bw_max[tid] = (double)(int32_t)(k ^ 0x80000000u);
+            else sh.bw_maxf[tid] = fkey_inv(k);
+        }
+    } else {
+        for (int wi = 0; wi < wd.n; ++wi) {
+            T m = B::lowest();
+            if (own) m = width_max<T, false>(x, sh, buf, tid, wd.w[wi], R2, (T)0, &dummy);
+            if constexpr (Traits<T>::is_int) {
+                m = warp_maxi(m);
+                if (lane == 0) sh.wredi[wi][warp] = m;
+            } else {
+                m = warp_max(m);
+                if (lane == 0) sh.wred[wi][warp] = m;
+            }
+        }
+        __syncthreads();
+        // per-width block maxima: warp w reduces the warp maxima of widths w, w + NW, ...
+        for (int wi = warp; wi < wd.n; wi += NW) {
+            if constexpr (Traits<T>::is_int) {
+                const double Bw = (double)warp_maxi(lane < NW ? sh.wredi[wi][lane] : INT32_MIN);
+                if (lane == 0) sh.bw_max[wi] = Bw;
+            } else {
+                const float bf = warp_max(lane < NW ? sh.wred[wi][lane] : -INFINITY);
+                if (lane == 0) sh.bw_maxf[wi] = bf;
+            }
         }
     }
     __syncthreads();
@@ -1290,10 +1373,23 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     __syncthreads();
     // first argmax of the winning width, recomputed bit-identically
     T target;
-    if constexpr (Traits<T>::is_int) target = (T)warp_maxi(lane < NW ? sh.wredi[bw][lane] : INT32_MIN);
-    else target = (T)warp_max(lane < NW ? sh.wred[bw][lane] : -INFINITY);
     int first = -1;
-    if (own && madpos) (void)width_max<T, true>(x, sh, buf, tid, wd.w[bw], R2, target, &first);
+    if constexpr (C::DIST && Traits<T>::is_int) {
+        if constexpr (Traits<T>::is_int) target = (T)(int32_t)(sh.wkey[bw] ^ 0x80000000u);
+        else target = (T)fkey_inv(sh.wkey[bw]);
+        if (own && madpos) {
+            T c[R2];
+            const T* cb = buf + sidx(base_pos);
+#pragma unroll
+            for (int r = 0; r < R2; r += 4)
+                *reinterpret_cast<int4*>(&c[r]) = *reinterpret_cast<const int4*>(cb + r);
+            (void)width_max<T, true>(c, sh, buf, tid, wd.w[bw], R2, target, &first);
+        }
+    } else {
+        if constexpr (Traits<T>::is_int) target = (T)warp_maxi(lane < NW ? sh.wredi[bw][lane] : INT32_MIN);
+        else target = (T)warp_max(lane < NW ? sh.wred[bw][lane] : -INFINITY);
+        if (own && madpos) (void)width_max<T, true>(x, sh, buf, tid, wd.w[bw], R2, target, &first);
+    }
     int fpos = 0x7fffffff;
     if (first >= 0) {
         fpos = base_pos + first;
