@@ -551,9 +551,9 @@ def run_gpu(args):
 # DRAM bytes (read + write) per folded-profile bin of one base period's fold
 # and scoring launches on the search's own path: ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of the two fold passes and the scorer of survey entry
-# 4352 (P0 = 19977, M = 4096; bench.py --kernel entry), 1474.7 MB over
-# 4096 x 19977 bins.
-DRAM_BYTES_PER_BIN = 1474.7e6 / (4096 * 19977)
+# 4352 (P0 = 19977, M = 4096; bench.py --kernel entry), 1472.9 MB over
+# 4096 x 19977 bins (mean of four calls).
+DRAM_BYTES_PER_BIN = 1472.9e6 / (4096 * 19977)
 
 
 # ---------------------------------------------------------------------------

@@ -702,8 +702,15 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     int ibase = 0;
     if constexpr (Traits<T>::is_int) {
         ibase = (int)floorf(mean);
-        const double span = 8.0 * (double)sig / (double)NBK;
-        while ((double)(1ll << ish) < span && ish < 40) ++ish;
+        // the smallest ish with 2^ish >= span = 8 sig / NBK, from the exponent
+        // bits (span is exact in FP32: NBK is a power of two); no FP64, which
+        // every thread would otherwise issue for every profile
+        const float span = 8.0f * sig / (float)NBK;
+        if (span > 1.0f) {
+            const uint32_t b = __float_as_uint(span);
+            ish = (int)((b >> 23) & 0xffu) - 127 + ((b & 0x7fffffu) != 0u ? 1 : 0);
+            ish = ish < 40 ? ish : 40;
+        }
     }
     auto bucket_m = [&](T v) -> int {
         if constexpr (Traits<T>::is_int) return ibucket<NBK>((int)v, ibase, ish);
