@@ -285,6 +285,9 @@ def _stride_sample(rows, n_pick: int):
     return rows[idx], int(round(k))
 
 
+_CPU_INPUTS = {}  # (n, workload maker) -> (series, octave series): generated once per process
+
+
 def cpu_oracle_sample(kw, n, make, budget_s: float):
     """Time the oracle on a bounded sample of the workload, on one thread and
     on every usable host core, and scale each to the whole plan by the FFA's
@@ -301,7 +304,12 @@ def cpu_oracle_sample(kw, n, make, budget_s: float):
     total_units = plan_units(rows)
     w_all = fold_adds(rows)
     w_total = float(w_all.sum())
-    x = make(7)
+    key = (n, make.__code__)
+    if key not in _CPU_INPUTS:
+        n_oct0 = int(rows["octave"].max()) + 1
+        # the octave series only feed the timing: white noise of each octave's length
+        _CPU_INPUTS[key] = (make(7), [np.random.default_rng(o).standard_normal(n >> o) for o in range(n_oct0)])
+    x, z = _CPU_INPUTS[key]
     sl = min(n, 1 << 20)
     raw = oracle.downsample(x[:sl], 1)
     t0 = time.perf_counter()
@@ -311,8 +319,6 @@ def cpu_oracle_sample(kw, n, make, budget_s: float):
     n_oct = int(rows["octave"].max()) + 1
     all_samples = sum(n >> o for o in range(n_oct))
     t_detrend = t_med * all_samples / sl
-    # the octave series only feed the timing: white noise of each octave's length
-    z = [np.random.default_rng(o).standard_normal(n >> o) for o in range(n_oct)]
     # calibrate on the cheapest base period: additions per second on one thread
     i0 = int(np.argmin(w_all))
     t0 = time.perf_counter()
