@@ -702,13 +702,16 @@ __global__ void __launch_bounds__(C::T, C::MINB) k_score2(const T* __restrict__ 
     int ibase = 0;
     if constexpr (Traits<T>::is_int) {
         ibase = (int)floorf(mean);
-        // the smallest ish with 2^ish >= span = 8 sig / NBK, from the exponent
-        // bits (span is exact in FP32: NBK is a power of two); no FP64, which
-        // every thread would otherwise issue for every profile
+        // bucket width 2^ish: the power of two nearest to span = 8 sig / NBK
+        // (the float buckets' width), within a factor sqrt(2) of it, so the
+        // median's bucket holds about as many samples as a float profile's;
+        // from the exponent and mantissa bits (span is exact in FP32: NBK is a
+        // power of two), without the FP64 that every thread would otherwise
+        // issue for every profile.  Any width gives a monotone bucket map.
         const float span = 8.0f * sig / (float)NBK;
         if (span > 1.0f) {
             const uint32_t b = __float_as_uint(span);
-            ish = (int)((b >> 23) & 0xffu) - 127 + ((b & 0x7fffffu) != 0u ? 1 : 0);
+            ish = (int)((b >> 23) & 0xffu) - 127 + ((b & 0x7fffffu) > 0x3504f3u ? 1 : 0);  // 0x3504f3: sqrt(2)'s
             ish = ish < 40 ? ish : 40;
         }
     }
